@@ -1,0 +1,336 @@
+"""Pins of the CPU oracle to things other than itself (no GPU needed).
+
+Each test ties an oracle function to a value the paper prints, a closed form,
+an independent exact method (exhaustive search, a DP along the other axis,
+path enumeration) or an algebraic law, so that a dropped term, a wrong index,
+a swapped operand or a wrong rule in the oracle fails at least one of them.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from conftest import read_golden
+
+INF = 0x3FFFFFFFFFFFFFFF
+LETTERS = "abcd"
+
+
+def word_str(m, code):
+    return "".join(LETTERS[(int(code) >> (2 * (m - i))) & 3] for i in range(1, m + 1))
+
+
+# ---------------------------------------------------------------- words (Definition 4, Table 1)
+
+def test_word_counts_match_table1(orc):
+    for m, cm in read_golden("paper_table1_counts.txt"):
+        assert orc.num_words(int(m)) == int(cm), f"m={m}"
+
+
+def test_words_by_string_search(orc):
+    # Definition 4 read as substring exclusion on the spelled-out word; weight 2 p(a) + p(b).
+    for m in range(1, 7):
+        code, wt = orc.words(m)
+        assert np.all(np.diff(code.astype(np.int64)) > 0)
+        spelled = [word_str(m, c) for c in code]
+        expected = ["".join(w) for w in itertools.product(LETTERS, repeat=m)
+                    if not any(f in "".join(w) for f in ("ad", "da", "ab", "ba", "bb"))]
+        assert spelled == expected
+        assert [2 * s.count("a") + s.count("b") for s in spelled] == list(wt)
+    assert orc.num_words(1) == 4
+
+
+# ---------------------------------------------------------------- transfer matrix (Sec. 4.A, Cor. 6)
+
+def test_transfer_m1_by_hand(orc):
+    rows = read_golden("transfer_m1_by_hand.txt")
+    expected = np.array([[INF if v == "inf" else int(v) for v in r] for r in rows], dtype=np.int64)
+    assert np.array_equal(orc.transfer(1), expected)
+
+
+def test_transfer_m2_hand_arcs(orc):
+    code, _ = orc.words(2)
+    idx = {word_str(2, c): i for i, c in enumerate(code)}
+    a = orc.transfer(2)
+    # q = "bd": row 1 (b) needs p_1 = d or (p_1 = c, p_2 = a); row 2 (d) needs p_2 = a.
+    # "da" is not a correct word, so the only successor is "ca", of weight 2.
+    row = a[idx["bd"]]
+    assert [w for w in idx if row[idx[w]] != INF] == ["ca"] and row[idx["ca"]] == 2
+    # q = "dd": both rows need an a below them: only "aa", weight 4.
+    row = a[idx["dd"]]
+    assert [w for w in idx if row[idx[w]] != INF] == ["aa"] and row[idx["aa"]] == 4
+    # q = "aa": each row allows a or c; "ac", "ca", "cc" and "aa" are all correct words.
+    row = a[idx["aa"]]
+    assert sorted(w for w in idx if row[idx[w]] != INF) == ["aa", "ac", "ca", "cc"]
+    assert row[idx["aa"]] == 4 and row[idx["ac"]] == 2 and row[idx["cc"]] == 0
+    # "cc" after "aa": each c has no a neighbour in p, but q = aa allows p = c outright.
+    # "cc" after "cc": needs a vertical a in p, which "cc" does not have.
+    assert a[idx["cc"], idx["cc"]] == INF
+
+
+# ---------------------------------------------------------------- (min,+) product (Sec. 3, Thm. 1)
+
+def test_minplus_worked_example(orc):
+    x = np.array([[0, 5], [INF, 1]], dtype=np.int64)
+    y = np.array([[2, INF], [0, 3]], dtype=np.int64)
+    # z00 = min(0+2, 5+0) = 2; z01 = min(inf, 5+3) = 8; z10 = min(inf, 1+0) = 1; z11 = min(inf, 1+3) = 4
+    assert orc.minplus(x, y).tolist() == [[2, 8], [1, 4]]
+    # the product is not commutative: y (x) x differs, so a transposed operand is caught
+    assert orc.minplus(y, x).tolist() == [[2, 7], [0, 4]]
+    # an all-infinite row stays infinite
+    x2 = np.array([[INF, INF], [0, 0]], dtype=np.int64)
+    assert orc.minplus(x2, y)[0].tolist() == [INF, INF]
+
+
+def test_minplus_is_shortest_walks(orc):
+    # Theorem 1: (A^k)_ij is the least label of a walk of length k from i to j.
+    rng = np.random.default_rng(7)
+    n = 6
+    a = np.where(rng.random((n, n)) < 0.45, rng.integers(0, 9, (n, n)), INF).astype(np.int64)
+    for k in (1, 2, 3, 4):
+        best = np.full((n, n), INF, dtype=np.int64)
+        for walk in itertools.product(range(n), repeat=k + 1):
+            lab = 0
+            for u, v in zip(walk, walk[1:]):
+                if a[u, v] == INF:
+                    lab = INF
+                    break
+                lab += int(a[u, v])
+            if lab < best[walk[0], walk[-1]]:
+                best[walk[0], walk[-1]] = lab
+        p = a.copy()
+        for _ in range(k - 1):
+            p = orc.minplus(p, a)
+        assert np.array_equal(p, best), f"k={k}"
+
+
+def test_minplus_identity_and_associativity(orc):
+    rng = np.random.default_rng(3)
+    n = 9
+    eye = np.full((n, n), INF, dtype=np.int64)
+    np.fill_diagonal(eye, 0)
+    mats = [np.where(rng.random((n, n)) < 0.5, rng.integers(0, 30, (n, n)), INF).astype(np.int64) for _ in range(3)]
+    x, y, z = mats
+    assert np.array_equal(orc.minplus(x, eye), x)
+    assert np.array_equal(orc.minplus(eye, x), x)
+    assert np.array_equal(orc.minplus(orc.minplus(x, y), z), orc.minplus(x, orc.minplus(y, z)))
+    # scalar law of Sec. 3: A (x) (alpha (x) B) = alpha (x) (A (x) B)
+    yb = np.where(y == INF, INF, y + 11)
+    lhs = orc.minplus(x, yb)
+    rhs = orc.minplus(x, y)
+    assert np.array_equal(lhs, np.where(rhs == INF, INF, rhs + 11))
+
+
+def test_minplus_rectangular(orc):
+    rng = np.random.default_rng(5)
+    x = np.where(rng.random((3, 5)) < 0.6, rng.integers(0, 9, (3, 5)), INF).astype(np.int64)
+    y = np.where(rng.random((5, 4)) < 0.6, rng.integers(0, 9, (5, 4)), INF).astype(np.int64)
+    z = orc.minplus(x, y)
+    for i in range(3):
+        for j in range(4):
+            terms = [int(x[i, t] + y[t, j]) for t in range(5) if x[i, t] != INF and y[t, j] != INF]
+            assert z[i, j] == (min(terms) if terms else INF)
+
+
+def test_minplus_i16_encoding(orc):
+    rng = np.random.default_rng(11)
+    for (r, k, c) in [(1, 7, 5), (13, 17, 9), (33, 33, 33)]:
+        x = np.where(rng.random((r, k)) < 0.5, 0x3FFF, rng.integers(0, 0x2000, (r, k))).astype(np.int16)
+        y = np.where(rng.random((k, c)) < 0.5, 0x3FFF, rng.integers(0, 0x2000, (k, c))).astype(np.int16)
+        x64 = np.where(x == 0x3FFF, np.int64(INF), x.astype(np.int64))
+        y64 = np.where(y == 0x3FFF, np.int64(INF), y.astype(np.int64))
+        z64 = orc.minplus(x64, y64)
+        z16 = orc.minplus_i16(x, y)
+        assert np.array_equal(np.where(z64 == INF, 0x3FFF, z64), z16)
+        ri = rng.integers(0, r, 10)
+        cj = rng.integers(0, c, 10)
+        assert np.array_equal(orc.minplus_i16_entries(x, y, ri, cj), z16[ri, cj])
+
+
+def test_power_step_is_the_product(orc):
+    for m in (2, 3, 4):
+        a = orc.transfer(m)
+        p = orc.minplus(a, a)
+        assert np.array_equal(orc.power_step(a, a), p)
+        assert np.array_equal(orc.power_step(p, a), orc.minplus(p, a))
+
+
+def test_power_rows_are_rows_of_powers(orc):
+    m = 4
+    a = orc.transfer(m)
+    rows = [0, 5, 50, 96]
+    got = orc.power_rows(m, rows, 6)
+    p = a.copy()
+    for k in range(1, 7):
+        assert np.array_equal(got[k - 1], p[rows]), f"k={k}"
+        p = orc.minplus(p, a)
+
+
+# ---------------------------------------------------------------- gamma_R (Cor. 6) against the definition
+
+@pytest.mark.parametrize("m,nmax", [(1, 18), (2, 10), (3, 8), (4, 6), (5, 5), (6, 4)])
+def test_gamma_matches_brute_force(orc, m, nmax):
+    g = orc.gamma_direct(m, nmax)
+    for n in range(3, nmax + 1):
+        assert g[n] == orc.brute_force(m, n), f"m={m} n={n}"
+
+
+def test_gamma_matches_row_dp(orc):
+    for m in range(1, 8):
+        g = orc.gamma_direct(m, 7)
+        for n in range(3, 8):
+            assert g[n] == orc.row_dp(m, n), f"m={m} n={n}"
+
+
+def test_row_dp_matches_brute_force(orc):
+    for m, n in [(1, 9), (2, 7), (3, 6), (4, 5), (5, 4), (6, 3)]:
+        assert orc.row_dp(m, n) == orc.brute_force(m, n)
+
+
+def test_cycle_closed_form(orc):
+    # gamma_R(C_n) = ceil(2n/3) (Cockayne et al., 2004); P_1 box C_n is the cycle C_n.
+    g = orc.gamma_direct(1, 60)
+    for n in range(3, 61):
+        assert g[n] == math.ceil(2 * n / 3)
+    for n in range(3, 10):
+        assert orc.row_dp(1, n) == math.ceil(2 * n / 3)
+
+
+def check_rdf(grid):
+    """The definition of Sec. 1 on P_m box C_n, on a grid of values f(row, col)."""
+    m, n = len(grid), len(grid[0])
+    for r in range(m):
+        for c in range(n):
+            if grid[r][c] != 0:
+                continue
+            nbrs = [(r, (c + 1) % n), (r, (c - 1) % n)]
+            if r > 0:
+                nbrs.append((r - 1, c))
+            if r < m - 1:
+                nbrs.append((r + 1, c))
+            if not any(grid[a][b] == 2 for a, b in nbrs):
+                return False
+    return True
+
+
+def test_p7c6_erratum(orc):
+    grid = [[int(v) for v in row] for row in read_golden("p7c6_rdf_weight20.txt")]
+    assert len(grid) == 7 and len(grid[0]) == 6
+    assert check_rdf(grid) and sum(map(sum, grid)) == 20
+    assert orc.row_dp(7, 6) == 20
+    assert orc.gamma_direct(7, 6)[6] == 20
+
+
+# ---------------------------------------------------------------- periods (Lemma 2, Prop. 7, Table 2)
+
+def _paper_triple_implied(ours, paper):
+    k, p, q = ours
+    n0, alpha, beta = paper
+    return k <= n0 and alpha % p == 0 and q * (alpha // p) == beta
+
+
+@pytest.mark.parametrize("m", [2, 3, 4, 5, 6, 7])
+def test_periods_match_table2(orc, m):
+    table = {int(r[0]): tuple(map(int, r[1:])) for r in read_golden("paper_table2_periods.txt")}
+    r = orc.power_until_periodic(m, kmax=40)
+    assert r["found"]
+    ours = (r["k"], r["p"], r["q"])
+    if m == 4:
+        # the first repeat is A^17 = 2 (x) A^16; Table 2's (16, 5, 10) follows from it by Lemma 2
+        assert ours == (16, 1, 2)
+    else:
+        assert ours == table[m]
+    assert _paper_triple_implied(ours, table[m])
+
+
+@pytest.mark.slow
+def test_period_m8_matches_table2(orc):
+    r = orc.power_until_periodic(8, kmax=30)
+    assert r["found"] and (r["k"], r["p"], r["q"]) == (21, 5, 18)
+    g = r["gamma"]
+    assert g[3] == 13  # the printed closed form gives 12 at n = 3 (erratum)
+    for n in range(4, r["j"] + 1):
+        assert g[n] == _paper_m8(n), f"n={n}"
+
+
+def test_lemma2_holds_beyond_the_repeat(orc):
+    for m in (2, 3, 5):
+        r = orc.power_until_periodic(m, kmax=40)
+        a = orc.transfer(m)
+        powers = {1: a}
+        for k in range(2, r["j"] + 4):
+            powers[k] = orc.power_step(powers[k - 1], a)
+        k, p, q = r["k"], r["p"], r["q"]
+        for t in range(0, 4):
+            lo, hi = powers[k + t], powers[k + p + t]
+            assert np.array_equal(np.where(lo == INF, INF, lo + q), hi)
+        # no earlier pair repeats (first-repeat rule)
+        for j in range(2, k + p):
+            for i in range(1, j):
+                d = powers[j] - powers[i]
+                fin = powers[i] != INF
+                same = np.array_equal(fin, powers[j] != INF) and len(set(d[fin].tolist())) <= 1
+                assert not same, (m, i, j)
+
+
+def test_gamma_from_period_extends_direct(orc):
+    for m in range(1, 7):
+        r = orc.power_until_periodic(m, kmax=40)
+        direct = orc.gamma_direct(m, 70)
+        for n in range(3, 71):
+            assert orc.gamma_from_period(r["gamma"], r["k"], r["p"], r["q"], n) == direct[n]
+
+
+def test_normalised_spread_fits_int16(orc):
+    # after subtracting the minimum, the finite entries of every power span at most 4m (and < 0x1FFF)
+    for m in range(1, 7):
+        a = orc.transfer(m)
+        p = a.copy()
+        for _ in range(30):
+            fin = p[p != INF]
+            assert fin.max() - fin.min() <= 4 * m < 0x1FFF
+            p = orc.power_step(p, a)
+
+
+# ---------------------------------------------------------------- closed forms of Sec. 4.C and Remark 13
+
+def _paper_m7(n):
+    return math.ceil(16 * n / 5) + (0 if n % 5 == 0 else 1)
+
+
+def _paper_m8(n):
+    base = math.ceil(18 * n / 5)
+    if n % 5 == 0:
+        return base
+    if n % 5 in (2, 3, 4) or n == 6:
+        return base + 1
+    return base + 2
+
+
+def _paper_m9(n):
+    return 4 * n if n % 5 == 0 else 4 * n + 2
+
+
+def test_closed_form_m7(orc):
+    g = orc.gamma_direct(7, 40)
+    for n in range(3, 41):
+        if n == 6:
+            assert g[n] == 20 and _paper_m7(n) == 21  # erratum of the printed formula
+        else:
+            assert g[n] == _paper_m7(n), f"n={n}"
+
+
+def test_closed_forms_small_n_row_dp(orc):
+    # m = 8, 9 at n = 3..7 by the independent path-direction DP
+    for n in range(3, 8):
+        v8, v9 = orc.row_dp(8, n), orc.row_dp(9, n)
+        assert v8 == (13 if n == 3 else _paper_m8(n)), f"m=8 n={n}"
+        assert v9 == _paper_m9(n), f"m=9 n={n}"
+
+
+def test_remark13(orc):
+    for m in range(4, 8):
+        g = orc.gamma_direct(m, 40)
+        for n in range(5, 41, 5):
+            assert 5 * g[n] == 2 * (m + 1) * n, (m, n)
