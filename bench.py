@@ -1,0 +1,333 @@
+"""Benchmark of the (min,+) power path on GB300.
+
+Prints ONE JSON line (rank 0).  Headline: add-min throughput of the (min,+)
+product C = A (x) B at N = 16384 (synthetic operands, int16, entries uniform in
+[0, 32], each infinite with probability 1/2, seeds 1 and 2), with inputs resident
+in HBM; the step is one rd_minplus_gemm call (DPX product + fused minimum
+reduction).  Operands (2 x 512 MiB) exceed the 129 MB L2, so no flush is needed
+between steps.  Beside it, in the same line:
+  * e2e: the same product through the C ABI with host operands, the pinned
+    host->device copies of A and B and the device->host copy of C inside the
+    timed region;
+  * roofline of the product kernel against the DPX add-min peak;
+  * time_to_period: the whole hot path (enumerate + build A(G), power until the
+    first repeat, gamma_R closed form) for m = 3, 7, 9, with the oracle's time;
+  * cpu_baseline: the oracle's product on a bounded sample of rows.
+
+--impl reference times the oracle (the plain CPU restatement of the method) on
+the same workload, one bounded row sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_HEAD = 16384
+SEED_A, SEED_B = 1, 2
+# DPX peak derived from unit counts and clock: 152 SMs x 64 __viaddmin_s16x2 lanes per clock
+# (measured 126.6 add-mins/clock/SM in a register-resident loop) x 2 add-mins per lane x 2070 MHz.
+SMS, DPX_LANES_PER_CLK, ADDMIN_PER_LANE, SM_MAX_MHZ = 152, 64, 2, 2070.0
+PEAK_GOPS = SMS * DPX_LANES_PER_CLK * ADDMIN_PER_LANE * SM_MAX_MHZ * 1e6 / 1e9
+# DRAM bytes (read + write) per launch of the product kernel at N = 16384 from the ncu capture
+# summarised in profiles/minplus_gemm_n16384.md; None until that capture matches the current kernel.
+GEMM_TRAFFIC_BYTES = None
+CONFIG_NAME = "synthetic dense (min,+) GEMM N=16384, int16 uniform[0,32], P(inf)=0.5"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.reader = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.reader is not None:
+                self.reader.join(timeout=2)
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline_gemm(a: np.ndarray, b: np.ndarray, rows: int) -> dict:
+    """The oracle's textbook product on the first `rows` rows of A against all of B."""
+    import oracle
+
+    n = b.shape[1]
+    t0 = time.perf_counter()
+    oracle.minplus_i16(a[:rows], b)
+    dt = time.perf_counter() - t0
+    ops = rows * a.shape[1] * n
+    return {"value": ops / dt / 1e9, "unit": "G add-min/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"rows 0..{rows - 1} of C = A (x) B at N={n} ({ops:.3g} add-mins, {dt:.1f} s)"}
+
+
+def closed_form(r: dict, n: int) -> int:
+    """gamma_R(n) from the boundary values and (k, p, q) (Prop. 7)."""
+    k, p, q = r["k"], r["p"], r["q"]
+    if n < k + p:
+        return int(r["gamma"][n])
+    return int(r["gamma"][k + (n - k) % p]) + q * ((n - k) // p)
+
+
+def time_to_period(rd, torch, ms: list[int], with_oracle: bool) -> dict:
+    """The whole hot path for each m: build A(G), power until periodic, closed form for n = 3..1000."""
+    out = {}
+    for m in ms:
+        n = rd.state_count(m)
+        ld = rd.padded_dim(n)
+        kmax = 64
+        work = rd.power_workspace(n, ld, kmax, 8)
+        A = torch.empty((n, ld), dtype=torch.int16, device="cuda")
+        # one untimed pass (first-touch of the allocations, module load), then the timed one
+        for timed in (False, True):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rd.build_transfer(m, A)
+            r = rd.power_until_periodic(A, n, kmax, work)
+            gam = [closed_form(r, nn) for nn in range(3, 1001)]
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        products = r["j"] - 1
+        entry = {"N": n, "k": r["k"], "p": r["p"], "q": r["q"], "products": products, "gpu_s": dt,
+                 "dense_addmin_gops": products * n ** 3 / dt / 1e9, "gamma_R_n3_to_12": gam[:10]}
+        if with_oracle:
+            import oracle
+
+            if m <= 7:
+                t0 = time.perf_counter()
+                o = oracle.power_until_periodic(m, kmax=kmax)
+                entry["oracle_s"] = time.perf_counter() - t0
+                entry["oracle_matches"] = bool(o["found"] and (o["k"], o["p"], o["q"]) == (r["k"], r["p"], r["q"]))
+            else:
+                rows = 16
+                t0 = time.perf_counter()
+                oracle.power_rows(m, np.arange(rows), r["j"])
+                dt_o = time.perf_counter() - t0
+                entry["oracle_s_extrapolated"] = dt_o * n / rows
+                entry["oracle_sample"] = f"rows 0..{rows - 1} of A^1..A^{r['j']} ({dt_o:.1f} s), scaled by N/{rows}"
+            entry["oracle_cores"] = oracle.threads()
+        out[f"m={m}"] = entry
+        del work, A
+    return out
+
+
+def run_reference(args, rank, world) -> None:
+    """--impl reference: the oracle on the same workload, one bounded row sample per step."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2409_17658_gb300 import inputs
+
+    n = N_HEAD
+    rows = 8
+    a = inputs.matrix(rows, n, seed=SEED_A)
+    b = inputs.matrix(n, n, seed=SEED_B)
+    for _ in range(args.warmup):
+        oracle.minplus_i16(a[:1], b)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.minplus_i16(a, b)
+    dt = time.perf_counter() - t0
+    ops = args.steps * rows * n * n
+    value = ops / dt / 1e9
+    line = {"metric": "(min,+) add-min GOPS and % of GB300 DPX/INT peak at N=16384; gamma_R time-to-period vs oracle",
+            "value": value, "unit": "G add-min/s", "impl": "reference", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": CONFIG_NAME, "N": n, "sample_rows_per_step": rows},
+            "cpu_baseline": {"value": value, "unit": "G add-min/s", "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"{rows} rows of C per step ({rows * n * n:.3g} add-mins)"},
+            "e2e": {"value": value, "unit": "G add-min/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-period", action="store_true", help="skip the time-to-period leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timings")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+
+    import paper_2409_17658_gb300 as rd
+    from paper_2409_17658_gb300 import build, inputs
+
+    build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    n = N_HEAD
+    a = inputs.matrix(n, n, seed=SEED_A)
+    b = inputs.matrix(n, n, seed=SEED_B)
+    A = torch.from_numpy(a).cuda()
+    B = torch.from_numpy(b).cuda()
+    C = torch.empty((n, n), dtype=torch.int16, device="cuda")
+    mn = torch.empty(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        rd.minplus_gemm(A, B, C, min_out=mn)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region: events around every launch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            rd.minplus_gemm(A, B, C, min_out=mn)
+            ev[i][1].record(stream)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    total_ms = start.elapsed_time(stop)
+    per_launch_ms = float(np.mean([s.elapsed_time(e) for s, e in ev]))
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ops_per_step = float(n) ** 3
+    value = world * args.steps * ops_per_step / (total_ms * 1e-3) / 1e9
+    clk = clocks.summary()
+
+    # ---- end to end through the C ABI with host buffers
+    a_pin = torch.from_numpy(a).pin_memory()
+    b_pin = torch.from_numpy(b).pin_memory()
+    c_pin = torch.empty((n, n), dtype=torch.int16).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        A.copy_(a_pin, non_blocking=True)
+        B.copy_(b_pin, non_blocking=True)
+        rd.minplus_gemm(A, B, C, min_out=mn)
+        c_pin.copy_(C, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * e2e_steps * ops_per_step / (e2e_ms * 1e-3) / 1e9
+    assert np.array_equal(c_pin[:2].numpy(), C[:2].cpu().numpy())
+
+    extra = {}
+    if rank == 0 and not args.no_period:
+        extra["time_to_period"] = time_to_period(rd, torch, [3, 7, 9], with_oracle=not args.no_cpu)
+    if rank == 0 and not args.no_cpu:
+        extra["cpu_baseline"] = cpu_baseline_gemm(a, b, rows=32)
+
+    if rank == 0:
+        achieved = ops_per_step / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": PEAK_GOPS, "unit": "G add-min/s",
+                "frac": achieved / PEAK_GOPS, "traffic": GEMM_TRAFFIC_BYTES,
+                "kernel": "minplus_gemm_kernel<false>", "per_launch_ms": per_launch_ms,
+                "peak_basis": "152 SMs x 64 DPX s16x2 lanes/clk x 2 add-min x 2070 MHz (derived; microbenchmark "
+                              "measured 126.6 add-min/clk/SM)"}
+        if clk.get("sm_mhz"):
+            roof["frac_at_sampled_clock"] = achieved / (PEAK_GOPS * clk["sm_mhz"] / SM_MAX_MHZ)
+        line = {"metric": "(min,+) add-min GOPS and % of GB300 DPX/INT peak at N=16384; gamma_R time-to-period vs oracle",
+                "value": value, "unit": "G add-min/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int16", "data": "synthetic",
+                "config": {"workload": CONFIG_NAME, "N": n, "seeds": [SEED_A, SEED_B], "parallelism": f"replicas{world}",
+                           "l2": "operands 2 x 512 MiB > 129 MB L2; no flush"},
+                "frac_of_peak": value / world / PEAK_GOPS,
+                "e2e": {"value": e2e_value, "unit": "G add-min/s", "h2d_bytes_per_step": 2 * a.nbytes,
+                        "d2h_bytes_per_step": a.nbytes, "steps": e2e_steps},
+                "gpu_launches": 2 * args.steps,
+                "roofline": roof, "clocks": clk}
+        line.update(extra)
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,160 @@
+/*
+ * rd.h -- C ABI of the GB300 (sm_103a) library for the Roman domination number
+ * of cylinders P_m box C_n by (min,+) matrix powers (arXiv 2409.17658).
+ *
+ * Method (Sec. 4.A-4.B of the paper): the columns of a Roman dominating
+ * function are "correct words" over {a,b,c,d} (Definition 4); the digraph G on
+ * those words has an arc q -> p when p can follow q, labelled with the weight
+ * 2 p(a) + p(b) of p.  With A = A(G), gamma_R(P_m box C_n) = min_p (A^n)_pp
+ * (Corollary 6), and a relation A^(k+p) = q (x) A^k fixes gamma_R for every
+ * larger n (Lemma 2, Prop. 7).
+ *
+ * Conventions shared by every entry point:
+ *  - Matrices are dense, row-major int16 in device memory, with a leading
+ *    dimension (ld, in elements) that must be a multiple of 8 and >= the
+ *    number of columns; base pointers must be 16-byte aligned.
+ *  - RD_INF (0x3FFF) encodes the tropical infinity.  Every other operand entry
+ *    must be finite and lie in [0, RD_MAX_FINITE]; then a + b never wraps in
+ *    int16 and a product entry is finite exactly when some finite + finite
+ *    term exists.  Product entries are clamped to RD_INF.
+ *  - The caller owns every buffer; unless stated otherwise a call allocates no
+ *    device memory.  Device buffers may come from any allocator (PyTorch's
+ *    caching allocator in the Python binding).
+ *  - Calls are asynchronous on the given stream unless stated otherwise.
+ *    Errors are returned as rd_status; no call aborts, throws or exits.
+ *  - Word order: word p_1..p_m (row 1 first) has code sum_i letter(p_i) 4^(m-i)
+ *    with a=0, b=1, c=2, d=3; states are numbered in increasing code order
+ *    (lexicographic, a < b < c < d).  The paper fixes no order; gamma_R and
+ *    the period do not depend on it.
+ */
+#ifndef RD_H
+#define RD_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RD_OK = 0,
+  RD_ERR_ARG = 1,     /* bad argument: size, pointer alignment, m or n out of range */
+  RD_ERR_RANGE = 2,   /* an entry left [0, RD_MAX_FINITE] after normalisation: int16 no longer exact */
+  RD_ERR_NOMEM = 3,   /* caller's work buffer too small (or, for rd_gamma_R, a failed allocation) */
+  RD_ERR_CUDA = 4,    /* a CUDA runtime call failed; see rd_last_cuda_error() */
+  RD_NOT_FOUND = 5,   /* no relation A^(k+p) = q (x) A^k with k + p <= kmax (Algorithm 2's "not found") */
+  RD_ERR_TIMEOUT = 6  /* reserved for bounded device-side waits */
+} rd_status;
+
+#define RD_INF ((int16_t)0x3FFF)
+#define RD_MAX_FINITE 0x1FFF
+#define RD_MAX_M 15                 /* codes are 2 bits per row in a uint32 */
+#define RD_GAMMA_UNSET INT64_MIN    /* gamma slots that were not computed */
+#define RD_GAMMA_INF INT64_MAX      /* min diag(A^k) when every diagonal entry is infinite */
+
+/* Text of the last CUDA error seen by this library in the calling thread ("" if none). */
+const char *rd_last_cuda_error(void);
+
+/*
+ * rd_state_count -- C_m, the number of correct words of length m
+ * (Definition 4; Table 1 of Sec. 4.C lists m = 2..11).  Host-only, exact.
+ * m in [1, RD_MAX_M] else RD_ERR_ARG.
+ */
+rd_status rd_state_count(int m, int64_t *N);
+
+/* rd_padded_dim -- the smallest leading dimension >= N accepted by the library (N rounded up to 8). */
+rd_status rd_padded_dim(int64_t N, int64_t *Np);
+
+/*
+ * rd_enumerate_states -- the correct words of length m (Definition 4), in the
+ * word order above: codes_dev[r] = code of the r-th word, weights_dev[r] =
+ * 2 p(a) + p(b) (the arc label of Sec. 4.A).  Both device arrays hold C_m
+ * entries.  One thread per word unranks its code directly (no scan, no
+ * scratch).  RD_ERR_ARG for a bad m or null pointers.
+ */
+rd_status rd_enumerate_states(int m, uint32_t *codes_dev, uint8_t *weights_dev, cudaStream_t s);
+
+/*
+ * rd_build_transfer -- the transfer matrix A(G) of Corollary 6:
+ * A[q][p] = 2 p(a) + p(b) when word p can follow word q under the row rules of
+ * Sec. 4.A, else RD_INF.  Writes rows 0..C_m-1 and columns 0..lda-1 of A_dev
+ * (columns C_m..lda-1 are RD_INF).  A_dev holds C_m x lda int16, lda a multiple
+ * of 8 and >= C_m.  Readings where the paper is garbled or silent: the
+ * intermediate-row rules' "or p_1 = d" is read as p_i = d; for m = 1 there is
+ * no vertical neighbour, so "p_i = c and a neighbour is a" never holds.
+ */
+rd_status rd_build_transfer(int m, int16_t *A_dev, int64_t lda, cudaStream_t s);
+
+/*
+ * rd_minplus_gemm -- C = A (x) B, the (min,+) product of Sec. 3:
+ * C[i][j] = min_t (A[i][t] + B[t][j]), for an M x K matrix A, a K x N matrix B
+ * and an M x N result C (C may not alias A or B).  Operands follow the
+ * conventions above; result entries with no finite term are RD_INF (K = 0
+ * gives an all-RD_INF C).  Runs on the DPX add-min units (__viaddmin_s16x2).
+ * min_out, if not null, is a device int32 that receives min_ij C[i][j]
+ * (RD_INF when C has no finite entry); it is written by this call.
+ * RD_ERR_ARG for bad sizes, strides or alignment.
+ */
+rd_status rd_minplus_gemm(const int16_t *A, int64_t lda, const int16_t *B, int64_t ldb, int16_t *C, int64_t ldc,
+                          int64_t M, int64_t N, int64_t K, int32_t *min_out, cudaStream_t s);
+
+/*
+ * rd_power_work_bytes -- size of the work buffer rd_power_until_periodic needs
+ * to keep `slots` normalised powers (slots >= 2) of an N x N matrix with
+ * leading dimension ld, for at most kmax powers.  A relation with period p
+ * is verified only if slots > p.
+ */
+rd_status rd_power_work_bytes(int64_t N, int64_t ld, int kmax, int slots, size_t *bytes);
+
+/*
+ * rd_power_until_periodic -- Algorithm 2 of Sec. 4.B with the first-repeat
+ * rule.  For k = 1, 2, ... it forms the normalised power P_k = A^k - o_k
+ * (o_k = min A^k, kept exactly in int64; P_k has minimum 0), records
+ * gamma_host[k] = min_p (A^k)_pp = o_k + min diag P_k (Corollary 6; it is
+ * gamma_R(P_m box C_k) for k >= 3 when A is a transfer matrix), and stops at
+ * the smallest j for which P_j = P_i for some i < j, i.e. A^j = q (x) A^i with
+ * q = o_j - o_i (Lemma 2): then *k_out = i, *p_out = j - i, *q_out = q.
+ *   A_dev: N x N operand (lda), entries in [0, RD_MAX_FINITE] or RD_INF.
+ *   work_dev / work_bytes: caller-owned device scratch of at least
+ *     rd_power_work_bytes(N, lda, kmax, 2) bytes, 256-byte aligned; the ring
+ *     holds as many powers as fit.  Contents on entry are ignored.
+ *   gamma_host: host array of kmax + 1 int64; entries 1..j are written (j =
+ *     k + p, or kmax when no relation was found); the others are RD_GAMMA_UNSET.
+ * Returns RD_OK (relation found), RD_NOT_FOUND (none with j <= kmax; gamma
+ * entries 1..kmax are valid), RD_ERR_RANGE (a normalised power left
+ * [0, RD_MAX_FINITE]), RD_ERR_NOMEM (the ring was too short to hold the
+ * matching power P_i), RD_ERR_ARG or RD_ERR_CUDA.  The call synchronises the
+ * stream before returning; all host outputs are valid on return.
+ */
+rd_status rd_power_until_periodic(const int16_t *A_dev, int64_t N, int64_t lda, int kmax, void *work_dev,
+                                  size_t work_bytes, int64_t *gamma_host, int32_t *k_out, int32_t *p_out,
+                                  int64_t *q_out, cudaStream_t s);
+
+/*
+ * rd_power_slot -- byte offset, from the start of work_dev, of the normalised
+ * power P_k left in the ring by rd_power_until_periodic (same N, lda, kmax and
+ * work_bytes).  On return from that call the last `slots` powers computed are
+ * resident: P_k for last - slots < k <= last, where last = k_out + p_out when a
+ * relation was found.  The matrix there is N x lda int16 with min entry 0;
+ * A^k = o_k (x) P_k.  RD_ERR_ARG when k < 1 or the arguments describe no ring.
+ */
+rd_status rd_power_slot(int64_t N, int64_t lda, int kmax, size_t work_bytes, int k, size_t *byte_offset);
+
+/*
+ * rd_gamma_R -- gamma_R(P_m box C_n) for m in [1, RD_MAX_M], n >= 3 (C_n needs
+ * n >= 3).  The first call for a given m builds A(G) and runs
+ * rd_power_until_periodic on the current device, in device memory this call
+ * allocates and frees; the result (gamma for n < k + p, and (k, p, q)) is
+ * cached per m for the life of the process, and later calls evaluate the
+ * solution of the finite-difference equation of Prop. 7 on the host:
+ * gamma(n) = gamma(k + (n - k) mod p) + q floor((n - k) / p) for n >= k.
+ * Thread-safe.  Synchronous.
+ */
+rd_status rd_gamma_R(int m, int64_t n, int64_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RD_H */

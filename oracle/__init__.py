@@ -73,6 +73,8 @@ def _load():
             lib.rdo_row_dp.restype = i64
             lib.rdo_gamma_direct.argtypes = [ctypes.c_int, ctypes.c_int, vp]
             lib.rdo_gamma_direct.restype = ctypes.c_int
+            lib.rdo_transfer_rows.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp]
+            lib.rdo_transfer_rows.restype = ctypes.c_int
             _ = i32
             _lib = lib
     return _lib
@@ -118,6 +120,14 @@ def transfer(m: int) -> np.ndarray:
     rc = _load().rdo_transfer(m, _ptr(a), n)
     assert rc == 0
     return a
+
+
+def transfer_rows(m: int, rows) -> np.ndarray:
+    """Rows `rows` of A(G), int64 with INF, without building the whole matrix."""
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.empty((len(rows), num_words(m)), dtype=np.int64)
+    assert _load().rdo_transfer_rows(m, _ptr(rows), len(rows), _ptr(out)) == 0
+    return out
 
 
 def minplus(x: np.ndarray, y: np.ndarray) -> np.ndarray:

@@ -507,3 +507,20 @@ int rdo_gamma_direct(int m, int nmax, int64_t *gamma) {
   free(A); free(X); free(Z); free(ptr); free(col); free(w);
   return 0;
 }
+
+/* Rows rows[r] of A(G) (Corollary 6), out[r*N + p], for sizes where the full matrix is too large. */
+int rdo_transfer_rows(int m, const int64_t *rows, int nrows, int64_t *out) {
+  int64_t N = rdo_num_words(m);
+  if (N <= 0) return 1;
+  uint32_t *code = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N);
+  int32_t *wt = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+  if (!code || !wt) { free(code); free(wt); return 2; }
+  rdo_words(m, code, wt, N);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int r = 0; r < nrows; ++r)
+    for (int64_t p = 0; p < N; ++p)
+      out[(int64_t)r * N + p] = rdo_follows(m, code[rows[r]], code[p]) ? (int64_t)wt[p] : RDO_INF;
+  free(code);
+  free(wt);
+  return 0;
+}

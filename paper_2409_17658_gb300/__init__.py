@@ -1,0 +1,185 @@
+"""Python binding of the rd C ABI (include/rd.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library ``_build/librd.so``;
+this module converts torch tensors to pointers, sizes and the current CUDA
+stream, and converts status codes to exceptions.  It fails loudly when the
+library has not been built -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librd.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "rd.h")
+
+RD_OK, RD_ERR_ARG, RD_ERR_RANGE, RD_ERR_NOMEM, RD_ERR_CUDA, RD_NOT_FOUND, RD_ERR_TIMEOUT = range(7)
+STATUS_NAMES = {0: "RD_OK", 1: "RD_ERR_ARG", 2: "RD_ERR_RANGE", 3: "RD_ERR_NOMEM", 4: "RD_ERR_CUDA",
+                5: "RD_NOT_FOUND", 6: "RD_ERR_TIMEOUT"}
+RD_INF = 0x3FFF
+RD_MAX_FINITE = 0x1FFF
+RD_MAX_M = 15
+RD_GAMMA_UNSET = -(2 ** 63)
+RD_GAMMA_INF = 2 ** 63 - 1
+
+
+class RdError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = f"{where}: {STATUS_NAMES.get(status, status)}"
+        if status == RD_ERR_CUDA:
+            msg += f" ({_lib().rd_last_cuda_error().decode()})"
+        super().__init__(msg)
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2409_17658_gb300.build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        i64, i32, vp, sz = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t
+        st = ctypes.c_int
+        lib.rd_last_cuda_error.restype = ctypes.c_char_p
+        lib.rd_last_cuda_error.argtypes = []
+        lib.rd_state_count.argtypes = [ctypes.c_int, vp]
+        lib.rd_padded_dim.argtypes = [i64, vp]
+        lib.rd_enumerate_states.argtypes = [ctypes.c_int, vp, vp, vp]
+        lib.rd_build_transfer.argtypes = [ctypes.c_int, vp, i64, vp]
+        lib.rd_minplus_gemm.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, vp, vp]
+        lib.rd_power_work_bytes.argtypes = [i64, i64, ctypes.c_int, ctypes.c_int, vp]
+        lib.rd_power_until_periodic.argtypes = [vp, i64, i64, ctypes.c_int, vp, sz, vp, vp, vp, vp, vp]
+        lib.rd_gamma_R.argtypes = [ctypes.c_int, i64, vp]
+        lib.rd_power_slot.argtypes = [i64, i64, ctypes.c_int, sz, ctypes.c_int, vp]
+        for name in ("rd_state_count", "rd_padded_dim", "rd_enumerate_states", "rd_build_transfer",
+                     "rd_minplus_gemm", "rd_power_work_bytes", "rd_power_until_periodic", "rd_gamma_R",
+                     "rd_power_slot"):
+            getattr(lib, name).restype = st
+        _ = i32
+        _LIB = lib
+    return _LIB
+
+
+def declared_symbols() -> list[str]:
+    """Names of the functions include/rd.h declares."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:rd_status|const char \*)\s*(rd_\w+)\s*\(", text, re.M)))
+
+
+def _check(status: int, where: str, ok=(RD_OK,)):
+    if status not in ok:
+        raise RdError(status, where)
+    return status
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t) -> ctypes.c_void_p:
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- entry points (same names as the ABI)
+
+def state_count(m: int) -> int:
+    """C_m, the number of correct words of length m (Definition 4)."""
+    n = ctypes.c_int64()
+    _check(_lib().rd_state_count(m, ctypes.byref(n)), "rd_state_count")
+    return n.value
+
+
+def padded_dim(n: int) -> int:
+    """Smallest accepted leading dimension >= n."""
+    out = ctypes.c_int64()
+    _check(_lib().rd_padded_dim(n, ctypes.byref(out)), "rd_padded_dim")
+    return out.value
+
+
+def enumerate_states(m: int, codes, weights, stream=None) -> None:
+    """codes (int32/uint32, C_m) and weights (uint8, C_m) on the device."""
+    _check(_lib().rd_enumerate_states(m, _dptr(codes), _dptr(weights), _stream(stream)), "rd_enumerate_states")
+
+
+def build_transfer(m: int, A, stream=None) -> None:
+    """Fill A (int16, C_m x ld, row-major, ld = A.stride(0)) with A(G)."""
+    assert A.dim() == 2 and A.stride(1) == 1
+    _check(_lib().rd_build_transfer(m, _dptr(A), A.stride(0), _stream(stream)), "rd_build_transfer")
+
+
+def minplus_gemm(A, B, C, M: int | None = None, N: int | None = None, K: int | None = None, min_out=None,
+                 stream=None) -> None:
+    """C[:M, :N] = A[:M, :K] (x) B[:K, :N] on int16 CUDA tensors (row-major, unit column stride)."""
+    for t in (A, B, C):
+        assert t.dim() == 2 and t.stride(1) == 1
+    M = C.shape[0] if M is None else M
+    N = C.shape[1] if N is None else N
+    K = A.shape[1] if K is None else K
+    mo = _dptr(min_out) if min_out is not None else None
+    _check(_lib().rd_minplus_gemm(_dptr(A), A.stride(0), _dptr(B), B.stride(0), _dptr(C), C.stride(0), M, N, K,
+                                  mo, _stream(stream)), "rd_minplus_gemm")
+
+
+def power_work_bytes(n: int, ld: int, kmax: int, slots: int) -> int:
+    out = ctypes.c_size_t()
+    _check(_lib().rd_power_work_bytes(n, ld, kmax, slots, ctypes.byref(out)), "rd_power_work_bytes")
+    return out.value
+
+
+def power_until_periodic(A, n: int, kmax: int, work, stream=None) -> dict:
+    """Algorithm 2 on the device.  Returns dict(status, found, k, p, q, j, gamma (np.int64, index 1..j))."""
+    gamma = np.zeros(kmax + 1, dtype=np.int64)
+    k, p, q = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    st = _lib().rd_power_until_periodic(_dptr(A), n, A.stride(0), kmax, _dptr(work), work.numel() * work.element_size(),
+                                        ctypes.c_void_p(gamma.ctypes.data), ctypes.byref(k), ctypes.byref(p),
+                                        ctypes.byref(q), _stream(stream))
+    _check(st, "rd_power_until_periodic", ok=(RD_OK, RD_NOT_FOUND))
+    found = st == RD_OK
+    j = k.value + p.value if found else kmax
+    return dict(status=st, found=found, k=k.value if found else None, p=p.value if found else None,
+                q=q.value if found else None, j=j, gamma=gamma)
+
+
+def power_slot(n: int, ld: int, kmax: int, work_bytes: int, k: int) -> int:
+    """Byte offset of the resident normalised power P_k inside the work buffer."""
+    out = ctypes.c_size_t()
+    _check(_lib().rd_power_slot(n, ld, kmax, work_bytes, k, ctypes.byref(out)), "rd_power_slot")
+    return out.value
+
+
+def gamma_R(m: int, n: int) -> int:
+    """gamma_R(P_m box C_n), from the library's per-process cache."""
+    out = ctypes.c_int64()
+    _check(_lib().rd_gamma_R(m, n, ctypes.byref(out)), "rd_gamma_R")
+    return out.value
+
+
+# ---------------------------------------------------------------- allocation helpers (torch owns device memory)
+
+def transfer_matrix(m: int, device="cuda", stream=None):
+    """Allocate and build A(G); returns (A, N) with A of shape (N, ld)."""
+    import torch
+
+    n = state_count(m)
+    A = torch.empty((n, padded_dim(n)), dtype=torch.int16, device=device)
+    build_transfer(m, A, stream)
+    return A, n
+
+
+def power_workspace(n: int, ld: int, kmax: int, slots: int, device="cuda"):
+    import torch
+
+    return torch.empty(power_work_bytes(n, ld, kmax, slots), dtype=torch.uint8, device=device)

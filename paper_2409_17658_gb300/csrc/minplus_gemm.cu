@@ -1,0 +1,291 @@
+// minplus_gemm.cu -- C = A (x) B, C[i][j] = min_t (A[i][t] + B[t][j]) (Sec. 3),
+// on int16 operands with the DPX fused add-min __viaddmin_s16x2.
+//
+// Design (sm_103a):
+//  * Two output columns share one 32-bit register: acc = (C[i][j], C[i][j+1]).
+//    One DPX instruction updates both with min(a + b, acc), where b holds
+//    (B[t][j], B[t][j+1]) -- the natural packing of row-major B -- and a holds
+//    A[i][t] in both halfwords.  The duplication of A is done once per tile when
+//    it is staged into shared memory (A^T tile, one 32-bit word per element), so
+//    the inner loop is only 128-bit shared loads and DPX instructions.
+//  * On this part the DPX unit retires 64 lanes per clock per SM, half the issue
+//    rate, so the shared-memory loads and the loop overhead fit in the other half
+//    of the issue slots: the kernel is bound by the DPX pipe, not by memory.
+//  * CTA tile 128 x 256 x 32, 256 threads, 8 x 16 outputs (64 packed registers)
+//    per thread, two CTAs per SM.  B tiles are fetched with cp.async (16 B) into a
+//    3-stage ring; A tiles go through registers (prefetched one tile ahead) so
+//    they can be transposed and duplicated on the way into shared memory.
+//  * Ragged edges (M, N, K not multiples of the tile) are filled with RD_INF, the
+//    neutral element of min, so no padding is required of the caller.
+//  * No overflow: operands lie in [0, 0x1FFF] or are 0x3FFF, so every sum is at
+//    most 0x7FFE; accumulators start at RD_INF and only decrease, so an entry
+//    whose terms all involve RD_INF ends exactly at RD_INF.
+#include "rd_internal.cuh"
+
+namespace rd {
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 32, NT = 256;
+constexpr int BSTAGES = 3;
+constexpr int AS_WORDS = BK * BM;         // one A^T buffer, duplicated int16 -> 32-bit words
+constexpr int BS_WORDS = BK * (BN / 2);   // one B stage, packed int16 pairs
+constexpr size_t SMEM_BYTES = (size_t)(2 * AS_WORDS + BSTAGES * BS_WORDS) * 4;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack2(int16_t lo, int16_t hi) {
+  return (uint32_t)(uint16_t)lo | ((uint32_t)(uint16_t)hi << 16);
+}
+
+template <bool RING>
+__global__ void __launch_bounds__(NT, 2) minplus_gemm_kernel(GemmParams p) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t* As = smem;                 // [2][BK][BM]
+  uint32_t* Bs = smem + 2 * AS_WORDS;  // [BSTAGES][BK][BN/2]
+
+  const int16_t* __restrict__ Ag = p.A;
+  int16_t* __restrict__ Cg = p.C;
+  if (RING) {
+    const PowerState* st = p.st;
+    if (*(volatile const int32_t*)&st->done) return;
+    const int k = *(volatile const int32_t*)&st->k;
+    Ag = p.ring + (int64_t)(k % p.slots) * p.slot_elems;
+    Cg = p.ring + (int64_t)((k + 1) % p.slots) * p.slot_elems;
+  }
+  const int16_t* __restrict__ Bg = p.B;
+  const int64_t M = p.M, N = p.N, K = p.K, lda = p.lda, ldb = p.ldb, ldc = p.ldc;
+
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  const int KT = (int)((K + BK - 1) / BK);
+
+  // ---- staging helpers
+  uint4 areg[2];
+  auto load_a_regs = [&](int kt) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = tid + h * NT, row = c >> 2, kc = (c & 3) * 8;
+      const int64_t gi = m0 + row, gk = (int64_t)kt * BK + kc;
+      if (gi < M && gk + 8 <= K) {
+        areg[h] = __ldg(reinterpret_cast<const uint4*>(Ag + gi * lda + gk));
+      } else {
+        int16_t v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = (gi < M && gk + e < K) ? Ag[gi * lda + gk + e] : kInf;
+        areg[h] = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+      }
+    }
+  };
+  auto store_a_smem = [&](int buf) {
+    uint32_t* dst = As + buf * AS_WORDS;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = tid + h * NT, row = c >> 2, kc = (c & 3) * 8;
+      const uint32_t w[4] = {areg[h].x, areg[h].y, areg[h].z, areg[h].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        dst[(kc + 2 * q) * BM + row] = __byte_perm(w[q], 0, 0x1010);      // low half in both halves
+        dst[(kc + 2 * q + 1) * BM + row] = __byte_perm(w[q], 0, 0x3232);  // high half in both halves
+      }
+    }
+  };
+  auto load_b_stage = [&](int kt, int stage) {
+    uint32_t* dst = Bs + stage * BS_WORDS;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int c = tid + h * NT, kr = c >> 5, jc = (c & 31) * 8;
+      const int64_t gk = (int64_t)kt * BK + kr, gj = n0 + jc;
+      uint32_t* d = dst + kr * (BN / 2) + jc / 2;
+      if (gk < K && gj + 8 <= N) {
+        cp_async16(d, Bg + gk * ldb + gj);
+      } else {
+        int16_t v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = (gk < K && gj + e < N) ? Bg[gk * ldb + gj + e] : kInf;
+        *reinterpret_cast<uint4*>(d) =
+            make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+      }
+    }
+  };
+
+  uint32_t acc[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[r][c] = kInf2;
+
+  // ---- prologue
+#pragma unroll
+  for (int s = 0; s < BSTAGES - 1; ++s) {
+    if (s < KT) load_b_stage(s, s);
+    cp_async_commit();
+  }
+  if (KT > 0) {
+    load_a_regs(0);
+    store_a_smem(0);
+  }
+  if (KT > 1) load_a_regs(1);
+  cp_async_wait<BSTAGES - 2>();
+  __syncthreads();
+
+  // ---- main loop
+  for (int kt = 0; kt < KT; ++kt) {
+    {
+      const int nk = kt + BSTAGES - 1;
+      if (nk < KT) load_b_stage(nk, nk % BSTAGES);
+      cp_async_commit();
+    }
+    const uint32_t* a_s = As + (kt & 1) * AS_WORDS + ty * 8;
+    const uint32_t* b_s = Bs + (kt % BSTAGES) * BS_WORDS + tx * 4;
+#pragma unroll 8
+    for (int kk = 0; kk < BK; ++kk) {
+      const uint4 a0 = *reinterpret_cast<const uint4*>(a_s + kk * BM);
+      const uint4 a1 = *reinterpret_cast<const uint4*>(a_s + kk * BM + 4);
+      const uint4 b0 = *reinterpret_cast<const uint4*>(b_s + kk * (BN / 2));
+      const uint4 b1 = *reinterpret_cast<const uint4*>(b_s + kk * (BN / 2) + 64);
+      const uint32_t a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const uint32_t b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = __viaddmin_s16x2(a[r], b[c], acc[r][c]);
+    }
+    if (kt + 1 < KT) {
+      store_a_smem((kt + 1) & 1);
+      if (kt + 2 < KT) load_a_regs(kt + 2);
+    }
+    cp_async_wait<BSTAGES - 2>();
+    __syncthreads();
+  }
+
+  // ---- epilogue: store, and reduce the minimum and the diagonal minimum
+  uint32_t vmin = kInf2;
+  int32_t dmin = kInf;
+  const bool want_diag = (p.diag_out != nullptr) && (m0 < n0 + BN) && (n0 < m0 + BM);
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int64_t gi = m0 + ty * 8 + r;
+#pragma unroll
+    for (int part = 0; part < 2; ++part) {
+      const int64_t gj = n0 + part * 128 + tx * 8;
+      const uint32_t* w = &acc[r][part * 4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) vmin = __vmins2(vmin, w[c]);
+      if (gi < M) {
+        if (gj + 8 <= N) {
+          *reinterpret_cast<uint4*>(Cg + gi * ldc + gj) = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            if (gj + e < N) Cg[gi * ldc + gj + e] = (int16_t)((w[e >> 1] >> (16 * (e & 1))) & 0xFFFF);
+        }
+        if (want_diag && gi < N) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e)  // static indexes only, so acc stays in registers
+            if (gi == gj + e) dmin = min(dmin, (int32_t)((w[e >> 1] >> (16 * (e & 1))) & 0xFFFF));
+        }
+      }
+    }
+  }
+  if (p.min_out != nullptr || want_diag) {
+    int32_t lm = min((int32_t)(vmin & 0xFFFF), (int32_t)(vmin >> 16));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lm = min(lm, __shfl_xor_sync(0xFFFFFFFFu, lm, o));
+      dmin = min(dmin, __shfl_xor_sync(0xFFFFFFFFu, dmin, o));
+    }
+    __shared__ int32_t red_m[NT / 32], red_d[NT / 32];
+    if ((tid & 31) == 0) {
+      red_m[tid >> 5] = lm;
+      red_d[tid >> 5] = dmin;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int32_t bm = kInf, bd = kInf;
+      for (int w = 0; w < NT / 32; ++w) {
+        bm = min(bm, red_m[w]);
+        bd = min(bd, red_d[w]);
+      }
+      if (p.min_out != nullptr && bm < kInf) atomicMin(p.min_out, bm);
+      if (want_diag && bd < kInf) atomicMin(p.diag_out, bd);
+    }
+  }
+}
+
+__global__ void fill_i32_kernel(int32_t* dst, int32_t v) { *dst = v; }
+
+template <bool RING>
+cudaError_t set_smem_attr() {
+  static int done_dev[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done_dev[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(minplus_gemm_kernel<RING>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done_dev[dev] = 1;
+  return e;
+}
+
+}  // namespace
+
+cudaError_t launch_fill_i32(int32_t* dst, int32_t value, cudaStream_t s) {
+  fill_i32_kernel<<<1, 1, 0, s>>>(dst, value);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_minplus_gemm(const GemmParams& p, bool ring, cudaStream_t s) {
+  const int64_t gx = (p.N + BN - 1) / BN, gy = (p.M + BM - 1) / BM;
+  if (gx <= 0 || gy <= 0) return cudaSuccess;
+  if (gx > 0x7FFFFFFF || gy > 65535) return cudaErrorInvalidConfiguration;
+  const dim3 grid((unsigned)gx, (unsigned)gy);
+  cudaError_t e;
+  if (ring) {
+    e = set_smem_attr<true>();
+    if (e != cudaSuccess) return e;
+    minplus_gemm_kernel<true><<<grid, NT, SMEM_BYTES, s>>>(p);
+  } else {
+    e = set_smem_attr<false>();
+    if (e != cudaSuccess) return e;
+    minplus_gemm_kernel<false><<<grid, NT, SMEM_BYTES, s>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace rd
+
+using namespace rd;
+
+extern "C" rd_status rd_minplus_gemm(const int16_t* A, int64_t lda, const int16_t* B, int64_t ldb, int16_t* C,
+                                     int64_t ldc, int64_t M, int64_t N, int64_t K, int32_t* min_out,
+                                     cudaStream_t s) {
+  if (M < 0 || N < 0 || K < 0) return RD_ERR_ARG;
+  if (M > 0 && N > 0) {
+    if (!C || !aligned16(C) || ldc < N || ldc % 8 != 0) return RD_ERR_ARG;
+    if (K > 0) {
+      if (!A || !B || !aligned16(A) || !aligned16(B)) return RD_ERR_ARG;
+      if (lda < K || lda % 8 != 0 || ldb < N || ldb % 8 != 0) return RD_ERR_ARG;
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  if (min_out) {
+    e = launch_fill_i32(min_out, RD_INF, s);
+    if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
+  }
+  if (M == 0 || N == 0) return RD_OK;
+  GemmParams p{};
+  p.A = A; p.lda = lda; p.B = B; p.ldb = ldb; p.C = C; p.ldc = ldc;
+  p.M = M; p.N = N; p.K = K; p.min_out = min_out; p.diag_out = nullptr;
+  e = launch_minplus_gemm(p, false, s);
+  if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
+  return RD_OK;
+}

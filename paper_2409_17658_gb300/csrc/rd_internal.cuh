@@ -1,0 +1,80 @@
+// rd_internal.cuh -- definitions shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#include "rd.h"
+
+namespace rd {
+
+constexpr int16_t kInf = RD_INF;
+constexpr uint32_t kInf2 = 0x3FFF3FFFu;  // RD_INF in both halfwords
+constexpr int kMaxFinite = RD_MAX_FINITE;
+constexpr int kMaxCand = 8;
+
+// Device-resident bookkeeping of one rd_power_until_periodic run.  It lives at
+// the front of the caller's work buffer; the per-power arrays follow it.
+struct PowerState {
+  int32_t k;            // index of the latest finished normalised power P_k
+  int32_t done;         // 0 running, 1 relation found, 2 kmax reached, 3 error
+  int32_t err;          // bit 0 range, bit 1 ring too short, bit 2 too many hash candidates
+  int32_t kmax;
+  int32_t mu;           // atomicMin target: min of the raw product being formed
+  int32_t dmin;         // atomicMin target: min of its diagonal
+  uint32_t blocks_done; // arrival counter of the compare kernel
+  int32_t ncand;
+  int32_t cand[kMaxCand];
+  int32_t mismatch[kMaxCand];
+  int32_t found_i, found_j;
+  int64_t found_q;
+  unsigned long long hacc;  // hash accumulator of the power being normalised
+  int32_t range_bad;
+  int32_t slots;
+};
+
+constexpr size_t kStateHeader = 256;
+static_assert(sizeof(PowerState) <= kStateHeader, "state header too large");
+
+inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Layout of the work buffer: [header][offset int64 x (kmax+1)][gamma int64 x (kmax+1)]
+// [hash u64 x (kmax+1)] padded to 256 B, then the ring of power slots.
+inline size_t state_bytes(int kmax) { return round_up(kStateHeader + 3 * 8 * (size_t)(kmax + 1), 256); }
+inline size_t slot_bytes(int64_t N, int64_t ld) { return round_up((size_t)N * (size_t)ld * 2, 256); }
+
+__host__ __device__ inline int64_t* st_offset(PowerState* st) {
+  return reinterpret_cast<int64_t*>(reinterpret_cast<char*>(st) + kStateHeader);
+}
+__host__ __device__ inline int64_t* st_gamma(PowerState* st) { return st_offset(st) + (st->kmax + 1); }
+__host__ __device__ inline unsigned long long* st_hash(PowerState* st) {
+  return reinterpret_cast<unsigned long long*>(st_gamma(st) + (st->kmax + 1));
+}
+
+// Operands of one (min,+) product.  In ring mode the left operand and the
+// result are power slots chosen on the device from st->k.
+struct GemmParams {
+  const int16_t* A;
+  int64_t lda;
+  const int16_t* B;
+  int64_t ldb;
+  int16_t* C;
+  int64_t ldc;
+  int64_t M, N, K;
+  int32_t* min_out;   // nullable; atomicMin of all result entries
+  int32_t* diag_out;  // nullable; atomicMin of the diagonal entries
+  PowerState* st;     // ring mode only
+  int16_t* ring;
+  int64_t slot_elems;
+  int slots;
+};
+
+// Launchers implemented in the .cu files.
+cudaError_t launch_minplus_gemm(const GemmParams& p, bool ring, cudaStream_t s);
+cudaError_t launch_fill_i32(int32_t* dst, int32_t value, cudaStream_t s);
+
+void set_cuda_error(cudaError_t e);
+bool aligned16(const void* p);
+
+}  // namespace rd

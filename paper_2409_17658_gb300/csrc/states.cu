@@ -1,0 +1,207 @@
+// states.cu -- correct words (Definition 4) and the transfer matrix A(G)
+// (Sec. 4.A, Corollary 6) built on the GPU.
+//
+// Words are never materialised as a list on the device: each thread turns a
+// state index r into its code by unranking against a table T[len][letter] =
+// number of correct words of length len whose first letter is `letter`.  That
+// makes the enumerator one kernel with no scan and no scratch, and lets the
+// transfer builder regenerate the words of its tile in shared memory.
+#include <cstring>
+#include <string>
+
+#include "rd_internal.cuh"
+
+namespace rd {
+
+namespace {
+
+thread_local std::string g_last_error;
+
+// Definition 4 forbids the vertical factors ad, da, ab, ba, bb; `x` sits directly above `y`.
+__host__ __device__ inline bool pair_allowed(int x, int y) {
+  // bit (4*x + y) set = forbidden: ad(0,3) da(3,0) ab(0,1) ba(1,0) bb(1,1)
+  constexpr uint32_t forbidden = (1u << 3) | (1u << 12) | (1u << 1) | (1u << 4) | (1u << 5);
+  return ((forbidden >> (4 * x + y)) & 1u) == 0;
+}
+
+struct WordTable {
+  int m;
+  int64_t t[RD_MAX_M + 1][4];  // t[len][c]: correct words of length len starting with letter c
+};
+
+WordTable make_table(int m) {
+  WordTable w{};
+  w.m = m;
+  for (int c = 0; c < 4; ++c) w.t[1][c] = 1;
+  for (int len = 2; len <= m; ++len)
+    for (int c = 0; c < 4; ++c) {
+      int64_t s = 0;
+      for (int d = 0; d < 4; ++d)
+        if (pair_allowed(c, d)) s += w.t[len - 1][d];
+      w.t[len][c] = s;
+    }
+  return w;
+}
+
+// r-th correct word in lexicographic order (a < b < c < d, row 1 most significant).
+__device__ inline uint32_t unrank(const WordTable& w, int64_t r) {
+  uint32_t code = 0;
+  int prev = -1;
+  for (int i = 1; i <= w.m; ++i) {
+    const int len = w.m - i + 1;
+    for (int c = 0; c < 4; ++c) {
+      if (prev >= 0 && !pair_allowed(prev, c)) continue;
+      const int64_t cnt = w.t[len][c];
+      if (r < cnt) {
+        code = (code << 2) | (uint32_t)c;
+        prev = c;
+        break;
+      }
+      r -= cnt;
+    }
+  }
+  return code;
+}
+
+// Rows holding each letter, as bit masks (bit b = row m - b).
+struct Masks {
+  uint32_t a, b, c, d;
+};
+
+__device__ inline Masks word_masks(uint32_t code, int m) {
+  Masks k{0, 0, 0, 0};
+  for (int bit = 0; bit < m; ++bit) {
+    const uint32_t l = (code >> (2 * bit)) & 3u;
+    const uint32_t one = 1u << bit;
+    k.a |= (l == 0) ? one : 0u;
+    k.b |= (l == 1) ? one : 0u;
+    k.c |= (l == 2) ? one : 0u;
+    k.d |= (l == 3) ? one : 0u;
+  }
+  return k;
+}
+
+__device__ inline int word_weight(const Masks& k) { return 2 * __popc(k.a) + __popc(k.b); }
+
+// "p can follow q", all rows at once.  Row by row (Sec. 4.A):
+//   q_i = a -> p_i in {a, c}
+//   q_i = b -> p_i = d, or p_i = c with an a directly above or below it in p
+//   q_i = c -> p_i in {a, b, d}, or p_i = c with an a above or below it in p
+//   q_i = d -> p_i = a
+// The first and last rows have one vertical neighbour, which the shifts give
+// by construction; for m = 1 there is none.
+__device__ inline bool can_follow(const Masks& q, const Masks& p, uint32_t full) {
+  const uint32_t near_a = ((p.a << 1) | (p.a >> 1)) & full;
+  const uint32_t c_with_a = p.c & near_a;
+  const uint32_t bad = (q.a & ~(p.a | p.c)) | (q.b & ~(p.d | c_with_a)) |
+                       (q.c & ~(p.a | p.b | p.d | c_with_a)) | (q.d & ~p.a);
+  return bad == 0;
+}
+
+__global__ void enumerate_kernel(WordTable w, int64_t n, uint32_t* codes, uint8_t* weights) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const uint32_t code = unrank(w, r);
+  codes[r] = code;
+  weights[r] = (uint8_t)word_weight(word_masks(code, w.m));
+}
+
+// Tile of 64 rows (q) x 256 columns (p).  Thread (tx, ty): columns 8 tx .. 8 tx + 7,
+// rows ty, ty + 8, ..., one 16-byte store per row.
+constexpr int kTq = 64, kTp = 256;
+
+__global__ void __launch_bounds__(256) transfer_kernel(WordTable w, int64_t n, int16_t* A, int64_t lda,
+                                                       int64_t ptiles) {
+  __shared__ Masks qm[kTq];
+  __shared__ Masks pm[kTp];
+  __shared__ int16_t pw[kTp];
+  const int64_t tile = blockIdx.x;
+  const int64_t q0 = (tile / ptiles) * kTq, p0 = (tile % ptiles) * kTp;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < kTq + kTp; i += blockDim.x) {
+    if (i < kTq) {
+      const int64_t q = q0 + i;
+      qm[i] = (q < n) ? word_masks(unrank(w, q), w.m) : Masks{0, 0, 0, 0};
+    } else {
+      const int j = i - kTq;
+      const int64_t p = p0 + j;
+      if (p < n) {
+        pm[j] = word_masks(unrank(w, p), w.m);
+        pw[j] = (int16_t)word_weight(pm[j]);
+      } else {
+        pm[j] = Masks{0, 0, 0, 0};
+        pw[j] = kInf;
+      }
+    }
+  }
+  __syncthreads();
+  const uint32_t full = (w.m >= 32) ? 0xFFFFFFFFu : ((1u << w.m) - 1u);
+  const int tx = tid & 31, ty = tid >> 5;
+  const int64_t pc = p0 + 8 * tx;
+  if (pc >= lda) return;
+  for (int r = ty; r < kTq; r += 8) {
+    const int64_t q = q0 + r;
+    if (q >= n) break;
+    uint32_t packed[4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      const int j0 = 8 * tx + e, j1 = j0 + 1;
+      const int16_t v0 = (p0 + j0 < n && can_follow(qm[r], pm[j0], full)) ? pw[j0] : kInf;
+      const int16_t v1 = (p0 + j1 < n && can_follow(qm[r], pm[j1], full)) ? pw[j1] : kInf;
+      packed[e / 2] = (uint32_t)(uint16_t)v0 | ((uint32_t)(uint16_t)v1 << 16);
+    }
+    *reinterpret_cast<uint4*>(A + q * lda + pc) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+  }
+}
+
+}  // namespace
+
+void set_cuda_error(cudaError_t e) { g_last_error = cudaGetErrorString(e); }
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace rd
+
+using namespace rd;
+
+extern "C" const char* rd_last_cuda_error(void) { return g_last_error.c_str(); }
+
+extern "C" rd_status rd_state_count(int m, int64_t* N) {
+  if (m < 1 || m > RD_MAX_M || !N) return RD_ERR_ARG;
+  const WordTable w = make_table(m);
+  int64_t s = 0;
+  for (int c = 0; c < 4; ++c) s += w.t[m][c];
+  *N = s;
+  return RD_OK;
+}
+
+extern "C" rd_status rd_padded_dim(int64_t N, int64_t* Np) {
+  if (N < 0 || !Np) return RD_ERR_ARG;
+  *Np = (N + 7) / 8 * 8;
+  return RD_OK;
+}
+
+extern "C" rd_status rd_enumerate_states(int m, uint32_t* codes_dev, uint8_t* weights_dev, cudaStream_t s) {
+  int64_t n = 0;
+  if (rd_state_count(m, &n) != RD_OK || !codes_dev || !weights_dev) return RD_ERR_ARG;
+  const WordTable w = make_table(m);
+  const int threads = 256;
+  const int64_t blocks = (n + threads - 1) / threads;
+  enumerate_kernel<<<(unsigned)blocks, threads, 0, s>>>(w, n, codes_dev, weights_dev);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
+  return RD_OK;
+}
+
+extern "C" rd_status rd_build_transfer(int m, int16_t* A_dev, int64_t lda, cudaStream_t s) {
+  int64_t n = 0;
+  if (rd_state_count(m, &n) != RD_OK || !A_dev) return RD_ERR_ARG;
+  if (lda < n || lda % 8 != 0 || !aligned16(A_dev)) return RD_ERR_ARG;
+  const WordTable w = make_table(m);
+  const int64_t ptiles = (lda + kTp - 1) / kTp, qtiles = (n + kTq - 1) / kTq;
+  const int64_t tiles = ptiles * qtiles;
+  if (tiles > 0x7FFFFFFF) return RD_ERR_ARG;
+  transfer_kernel<<<(unsigned)tiles, 256, 0, s>>>(w, n, A_dev, lda, ptiles);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
+  return RD_OK;
+}

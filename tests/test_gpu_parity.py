@@ -1,0 +1,286 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, on a GB300.
+
+Integer work throughout, so every comparison is bit-exact.  Inputs are the
+transfer matrices of the paper (from the definition) and seeded synthetic
+operands from paper_2409_17658_gb300.inputs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from conftest import read_golden
+
+pytestmark = pytest.mark.gpu
+
+INF64 = 0x3FFFFFFFFFFFFFFF
+I16_INF = 0x3FFF
+
+
+@pytest.fixture(scope="module")
+def rd():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("these tests need a CUDA GPU")
+    from paper_2409_17658_gb300 import build
+
+    build.build()
+    import paper_2409_17658_gb300 as rd
+
+    return rd
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+
+    return torch
+
+
+def to_i16(a64):
+    return np.where(a64 == INF64, I16_INF, a64).astype(np.int16)
+
+
+def upload(torch, host, ld=None, junk=None):
+    """Copy a host int16 matrix into a device tensor of leading dimension ld (padding = junk or INF)."""
+    rows, cols = host.shape
+    ld = ld or ((cols + 7) // 8 * 8)
+    fill = I16_INF if junk is None else junk
+    t = torch.full((rows, ld), fill, dtype=torch.int16)
+    t[:, :cols] = torch.from_numpy(np.ascontiguousarray(host))
+    return t.cuda()
+
+
+# ---------------------------------------------------------------- a1: state enumerator
+
+@pytest.mark.parametrize("m", list(range(1, 12)))
+def test_enumerate_states(rd, torch_mod, orc, m):
+    torch = torch_mod
+    n = rd.state_count(m)
+    codes = torch.empty(n, dtype=torch.int32, device="cuda")
+    wts = torch.empty(n, dtype=torch.uint8, device="cuda")
+    rd.enumerate_states(m, codes, wts)
+    ocode, owt = orc.words(m)
+    assert np.array_equal(codes.cpu().numpy().view(np.uint32), ocode)
+    assert np.array_equal(wts.cpu().numpy().astype(np.int32), owt)
+
+
+# ---------------------------------------------------------------- a2: transfer matrix
+
+@pytest.mark.parametrize("m", list(range(1, 9)))
+def test_transfer_matrix(rd, torch_mod, orc, m):
+    A, n = rd.transfer_matrix(m)
+    got = A.cpu().numpy()
+    assert np.array_equal(got[:, :n], to_i16(orc.transfer(m)))
+    assert np.all(got[:, n:] == I16_INF)
+
+
+def test_transfer_matrix_m9_rows(rd, orc):
+    A, n = rd.transfer_matrix(9)
+    rng = np.random.default_rng(9)
+    rows = np.unique(np.concatenate([[0, 1, n // 2, n - 1], rng.integers(0, n, 28)]))
+    got = A[rows.tolist()].cpu().numpy()
+    assert np.array_equal(got[:, :n], to_i16(orc.transfer_rows(9, rows)))
+
+
+# ---------------------------------------------------------------- a3: (min,+) GEMM
+
+SHAPES = [(1, 1, 1), (7, 9, 5), (33, 33, 33), (128, 256, 32), (129, 257, 33), (300, 520, 700), (1, 777, 640),
+          (640, 8, 1000), (1000, 1000, 1000)]
+
+
+@pytest.mark.parametrize("dist", ["u32", "wide", "dense"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_minplus_gemm(rd, torch_mod, orc, shape, dist):
+    torch = torch_mod
+    from paper_2409_17658_gb300 import inputs
+
+    M, N, K = shape
+    a = inputs.matrix(M, K, seed=11, dist=dist)
+    b = inputs.matrix(K, N, seed=12, dist=dist)
+    # padding columns hold junk that a correct kernel never reads
+    A = upload(torch, a, ld=(K + 7) // 8 * 8 + 8, junk=-7)
+    B = upload(torch, b, ld=(N + 7) // 8 * 8 + 16, junk=-7)
+    C = torch.full((M, (N + 7) // 8 * 8), 12345, dtype=torch.int16, device="cuda")
+    mn = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rd.minplus_gemm(A, B, C, M, N, K, min_out=mn)
+    want = orc.minplus_i16(a, b)
+    got = C.cpu().numpy()
+    assert np.array_equal(got[:, :N].astype(np.int32), want)
+    assert np.all(got[:, N:] == 12345)  # nothing written past column N
+    assert mn.item() == want.min()
+
+
+def test_minplus_gemm_k0_and_empty(rd, torch_mod):
+    torch = torch_mod
+    A = torch.zeros((5, 8), dtype=torch.int16, device="cuda")
+    B = torch.zeros((8, 16), dtype=torch.int16, device="cuda")
+    C = torch.zeros((5, 16), dtype=torch.int16, device="cuda")
+    mn = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rd.minplus_gemm(A, B, C, 5, 16, 0, min_out=mn)
+    assert torch.all(C == I16_INF) and mn.item() == I16_INF
+    rd.minplus_gemm(A, B, C, 0, 16, 8)  # nothing to do
+    rd.minplus_gemm(A, B, C, 5, 0, 8)
+
+
+def test_minplus_gemm_all_infinite_rows(rd, torch_mod, orc):
+    torch = torch_mod
+    from paper_2409_17658_gb300 import inputs
+
+    a = inputs.matrix(200, 300, seed=21, dist="wide")
+    a[17, :] = I16_INF
+    b = inputs.matrix(300, 260, seed=22, dist="wide")
+    b[:, 100] = I16_INF
+    A, B = upload(torch, a), upload(torch, b)
+    C = torch.empty((200, 264), dtype=torch.int16, device="cuda")
+    rd.minplus_gemm(A, B, C, 200, 260, 300)
+    got = C.cpu().numpy()[:, :260]
+    assert np.all(got[17] == I16_INF) and np.all(got[:, 100] == I16_INF)
+    assert np.array_equal(got.astype(np.int32), orc.minplus_i16(a, b))
+
+
+@pytest.mark.parametrize("n", [4096, 16384])
+def test_minplus_gemm_full_size_sampled(rd, torch_mod, orc, n):
+    """Bench-size operands, 64 sampled entries (plus one full row and column) against the oracle."""
+    torch = torch_mod
+    from paper_2409_17658_gb300 import inputs
+
+    for dist, seeds in (("wide", (31, 32)), ("u32", (1, 2))):
+        a = inputs.matrix(n, n, seed=seeds[0], dist=dist)
+        b = inputs.matrix(n, n, seed=seeds[1], dist=dist)
+        A, B = upload(torch, a), upload(torch, b)
+        C = torch.empty((n, n), dtype=torch.int16, device="cuda")
+        rd.minplus_gemm(A, B, C)
+        rng = np.random.default_rng(n)
+        ri, cj = rng.integers(0, n, 64), rng.integers(0, n, 64)
+        got = C.cpu().numpy()
+        assert np.array_equal(got[ri, cj].astype(np.int32), orc.minplus_i16_entries(a, b, ri, cj))
+        r0 = int(rng.integers(0, n))
+        assert np.array_equal(got[r0].astype(np.int32), orc.minplus_i16(a[r0:r0 + 1], b)[0])
+        del A, B, C
+
+
+# ---------------------------------------------------------------- a4-a6: power driver
+
+def run_power(rd, torch, A, n, kmax, slots):
+    work = rd.power_workspace(n, A.stride(0), kmax, slots)
+    r = rd.power_until_periodic(A, n, kmax, work)
+    return r, work
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5, 6, 7])
+def test_power_until_periodic_matches_oracle(rd, torch_mod, orc, m):
+    A, n = rd.transfer_matrix(m)
+    r, work = run_power(rd, torch_mod, A, n, kmax=48, slots=8)
+    o = orc.power_until_periodic(m, kmax=48)
+    assert r["found"] and o["found"]
+    assert (r["k"], r["p"], r["q"]) == (o["k"], o["p"], o["q"])
+    assert np.array_equal(r["gamma"][1:r["j"] + 1], o["gamma"][1:o["j"] + 1])
+    assert np.all(r["gamma"][r["j"] + 1:] == rd.RD_GAMMA_UNSET)
+    if m <= 5:
+        # the resident powers are A^k - o_k exactly
+        a = orc.transfer(m)
+        powers = {1: a}
+        for k in range(2, r["j"] + 1):
+            powers[k] = orc.power_step(powers[k - 1], a)
+        ld = A.stride(0)
+        raw = work.cpu().numpy()
+        for k in range(r["j"] - 7, r["j"] + 1):
+            off = rd.power_slot(n, ld, 48, work.numel(), k)
+            pk = raw[off:off + n * ld * 2].view(np.int16).reshape(n, ld)[:, :n]
+            want = powers[k]
+            ok = want[want != INF64]
+            assert np.array_equal(pk, to_i16(np.where(want == INF64, INF64, want - ok.min()))), k
+
+
+def test_power_m8_matches_oracle(rd, torch_mod, orc):
+    A, n = rd.transfer_matrix(8)
+    r, _ = run_power(rd, torch_mod, A, n, kmax=30, slots=8)
+    o = orc.power_until_periodic(8, kmax=30)
+    assert (r["k"], r["p"], r["q"]) == (o["k"], o["p"], o["q"]) == (21, 5, 18)
+    assert np.array_equal(r["gamma"][1:r["j"] + 1], o["gamma"][1:o["j"] + 1])
+
+
+def test_power_m9_full_size(rd, torch_mod, orc):
+    """m = 9 (N = 21909): Table 2's triple, the row DP for n <= 7, and sampled rows of the resident powers."""
+    A, n = rd.transfer_matrix(9)
+    slots = 8
+    r, work = run_power(rd, torch_mod, A, n, kmax=40, slots=slots)
+    table = {int(x[0]): tuple(map(int, x[1:])) for x in read_golden("paper_table2_periods.txt")}
+    assert r["found"] and (r["k"], r["p"], r["q"]) == table[9]
+    g = r["gamma"]
+    for nn in range(3, 8):
+        assert g[nn] == orc.row_dp(9, nn)
+    # rows of the last resident powers equal rows of A^k up to one constant per power
+    rng = np.random.default_rng(99)
+    rows = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, 10)]))
+    ora = orc.power_rows(9, rows, r["j"])
+    ld = A.stride(0)
+    for k in range(r["j"] - slots + 1, r["j"] + 1):
+        off = rd.power_slot(n, ld, 40, work.numel(), k)
+        pk = work[off:off + n * ld * 2].view(torch_mod.int16).view(n, ld)[rows.tolist(), :n].cpu().numpy()
+        want = ora[k - 1]
+        fin = want != INF64
+        assert np.array_equal(pk == I16_INF, ~fin)
+        d = want[fin] - pk[fin].astype(np.int64)
+        assert np.all(d == d[0]) and pk[fin].min() >= 0, k
+
+
+def test_power_not_found_within_kmax(rd, torch_mod, orc):
+    A, n = rd.transfer_matrix(3)
+    r, _ = run_power(rd, torch_mod, A, n, kmax=9, slots=4)
+    assert r["status"] == rd.RD_NOT_FOUND and not r["found"]
+    assert np.array_equal(r["gamma"][1:10], orc.gamma_direct(3, 9)[1:10])
+
+
+def test_power_ring_too_short(rd, torch_mod):
+    A, n = rd.transfer_matrix(2)  # period 4 needs at least 5 slots
+    work = rd.power_workspace(n, A.stride(0), 40, 3)
+    with pytest.raises(rd.RdError) as e:
+        rd.power_until_periodic(A, n, 40, work)
+    assert e.value.status == rd.RD_ERR_NOMEM
+
+
+def test_power_range_violation(rd, torch_mod):
+    torch = torch_mod
+    A = torch.full((16, 16), 0x2000, dtype=torch.int16, device="cuda")  # entries above RD_MAX_FINITE
+    work = rd.power_workspace(16, 16, 8, 4)
+    with pytest.raises(rd.RdError) as e:
+        rd.power_until_periodic(A, 16, 8, work)
+    assert e.value.status == rd.RD_ERR_RANGE
+
+
+@pytest.mark.parametrize("n,seed", [(40, 1), (100, 2), (257, 3)])
+def test_power_synthetic_matrix(rd, torch_mod, orc, n, seed):
+    from paper_2409_17658_gb300 import inputs
+
+    a = inputs.matrix(n, n, seed=seed, dist="u32")
+    A = upload(torch_mod, a)
+    r, _ = run_power(rd, torch_mod, A, n, kmax=40, slots=41)
+    a64 = np.where(a == I16_INF, INF64, a.astype(np.int64))
+    o = orc.power_until_periodic(0, a=a64, kmax=40)
+    assert r["found"] == o["found"]
+    if o["found"]:
+        assert (r["k"], r["p"], r["q"]) == (o["k"], o["p"], o["q"])
+    assert np.array_equal(r["gamma"][1:o["j"] + 1], o["gamma"][1:o["j"] + 1])
+
+
+# ---------------------------------------------------------------- a7: closed-form evaluation
+
+def test_gamma_R_matches_algorithm1(rd, orc):
+    for m in range(1, 7):
+        direct = orc.gamma_direct(m, 70)
+        r = orc.power_until_periodic(m, kmax=48)
+        for n in range(3, 71):
+            assert rd.gamma_R(m, n) == direct[n], (m, n)
+        for n in (100, 1001, 12345):
+            assert rd.gamma_R(m, n) == orc.gamma_from_period(r["gamma"], r["k"], r["p"], r["q"], n)
+    for n in range(3, 200):
+        assert rd.gamma_R(1, n) == math.ceil(2 * n / 3)
+
+
+def test_gamma_R_closed_forms_m7(rd):
+    for n in range(3, 120):
+        want = 20 if n == 6 else math.ceil(16 * n / 5) + (0 if n % 5 == 0 else 1)
+        assert rd.gamma_R(7, n) == want, n

@@ -49,6 +49,11 @@ def test_transfer_m1_by_hand(orc):
     assert np.array_equal(orc.transfer(1), expected)
 
 
+def test_transfer_rows_are_rows(orc):
+    a = orc.transfer(4)
+    assert np.array_equal(orc.transfer_rows(4, [0, 17, 96]), a[[0, 17, 96]])
+
+
 def test_transfer_m2_hand_arcs(orc):
     code, _ = orc.words(2)
     idx = {word_str(2, c): i for i, c in enumerate(code)}
