@@ -211,6 +211,8 @@ def main() -> None:
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-period", action="store_true", help="skip the time-to-period leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timings")
+    ap.add_argument("--gemm-only", type=int, default=0, metavar="N",
+                    help="time only the product at size N (used for profiler captures)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -229,11 +231,9 @@ def main() -> None:
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    n = N_HEAD
-    a = inputs.matrix(n, n, seed=SEED_A)
-    b = inputs.matrix(n, n, seed=SEED_B)
-    A = torch.from_numpy(a).cuda()
-    B = torch.from_numpy(b).cuda()
+    n = args.gemm_only or N_HEAD
+    A = inputs.matrix_torch(n, n, seed=SEED_A, device="cuda")
+    B = inputs.matrix_torch(n, n, seed=SEED_B, device="cuda")
     C = torch.empty((n, n), dtype=torch.int16, device="cuda")
     mn = torch.empty(1, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -270,6 +270,13 @@ def main() -> None:
     ops_per_step = float(n) ** 3
     value = world * args.steps * ops_per_step / (total_ms * 1e-3) / 1e9
     clk = clocks.summary()
+    if args.gemm_only:
+        if rank == 0:
+            print(json.dumps({"gemm_only": n, "steps": args.steps, "ms_per_launch": per_launch_ms,
+                              "gops": ops_per_step / (per_launch_ms * 1e-3) / 1e9, "clocks": clk}))
+        return
+    a = A.cpu().numpy()
+    b = B.cpu().numpy()
 
     # ---- end to end through the C ABI with host buffers
     a_pin = torch.from_numpy(a).pin_memory()

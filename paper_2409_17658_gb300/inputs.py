@@ -81,6 +81,59 @@ def cols_of(col_idx, rows: int, cols: int, seed: int, dist: str = "u32") -> np.n
     return _values(splitmix64((np.uint64(seed) << np.uint64(32)) + idx), dist)
 
 
+# ---------------------------------------------------------------- the same stream with torch (CPU or CUDA)
+
+def _s64(u: int) -> int:
+    return u - (1 << 64) if u >= (1 << 63) else u
+
+
+def _srl(z, s: int):
+    """Logical right shift of an int64 tensor holding uint64 bits."""
+    return (z >> s) & ((1 << (64 - s)) - 1)
+
+
+def splitmix64_torch(counter):
+    """splitmix64() on an int64 torch tensor (uint64 bits, wrapping arithmetic)."""
+    z = (counter + 1) * _s64(0x9E3779B97F4A7C15)
+    z = (z ^ _srl(z, 30)) * _s64(0xBF58476D1CE4E5B9)
+    z = (z ^ _srl(z, 27)) * _s64(0x94D049BB133111EB)
+    return z ^ _srl(z, 31)
+
+
+def _values_torch(x, dist: str):
+    import torch
+
+    lo = x & 0xFFFFFFFF
+    if dist == "u32":
+        v = (lo * 33) >> 32
+        inf = x < 0
+    elif dist == "wide":
+        v = (lo * 0x2000) >> 32
+        inf = x < 0
+    elif dist == "dense":
+        v = (lo * 0x2000) >> 32
+        inf = torch.zeros_like(x, dtype=torch.bool)
+    else:
+        raise ValueError(dist)
+    return torch.where(inf, torch.full_like(v, INF16), v).to(torch.int16)
+
+
+def matrix_torch(rows: int, cols: int, seed: int, dist: str = "u32", ld: int | None = None, device="cpu",
+                 chunk_rows: int = 2048):
+    """Same values as matrix(), drawn with torch on `device` (a rows x ld int16 tensor)."""
+    import torch
+
+    ld = cols if ld is None else ld
+    out = torch.full((rows, ld), INF16, dtype=torch.int16, device=device)
+    base = seed << 32
+    col = torch.arange(cols, dtype=torch.int64, device=device)[None, :]
+    for r0 in range(0, rows, chunk_rows):
+        r1 = min(rows, r0 + chunk_rows)
+        idx = torch.arange(r0, r1, dtype=torch.int64, device=device)[:, None] * cols + col
+        out[r0:r1, :cols] = _values_torch(splitmix64_torch(idx + base), dist)
+    return out
+
+
 def log_uniform_sizes(count: int, lo: int, hi: int, seed: int) -> list[int]:
     """count sizes round(exp(U[ln lo, ln hi])) from the same counter-based stream."""
     x = splitmix64((np.uint64(seed) << np.uint64(32)) + np.arange(count, dtype=np.uint64))

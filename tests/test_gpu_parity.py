@@ -147,9 +147,10 @@ def test_minplus_gemm_full_size_sampled(rd, torch_mod, orc, n):
     from paper_2409_17658_gb300 import inputs
 
     for dist, seeds in (("wide", (31, 32)), ("u32", (1, 2))):
-        a = inputs.matrix(n, n, seed=seeds[0], dist=dist)
-        b = inputs.matrix(n, n, seed=seeds[1], dist=dist)
-        A, B = upload(torch, a), upload(torch, b)
+        A = inputs.matrix_torch(n, n, seed=seeds[0], dist=dist, device="cuda")
+        B = inputs.matrix_torch(n, n, seed=seeds[1], dist=dist, device="cuda")
+        a, b = A.cpu().numpy(), B.cpu().numpy()
+        assert np.array_equal(a[:3], inputs.matrix(3, n, seed=seeds[0], dist=dist))
         C = torch.empty((n, n), dtype=torch.int16, device="cuda")
         rd.minplus_gemm(A, B, C)
         rng = np.random.default_rng(n)

@@ -44,3 +44,12 @@ def test_log_uniform_sizes():
     s = inputs.log_uniform_sizes(64, 128, 8192, seed=9)
     assert len(s) == 64 and min(s) >= 128 and max(s) <= 8192
     assert s == inputs.log_uniform_sizes(64, 128, 8192, seed=9)
+
+
+def test_torch_stream_matches_numpy():
+    import torch
+
+    for dist in ("u32", "wide", "dense"):
+        a = inputs.matrix(45, 67, seed=7, dist=dist, ld=72)
+        t = inputs.matrix_torch(45, 67, seed=7, dist=dist, ld=72, chunk_rows=10)
+        assert t.dtype == torch.int16 and np.array_equal(t.numpy(), a)
