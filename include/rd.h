@@ -143,6 +143,36 @@ rd_status rd_power_until_periodic(const int16_t *A_dev, int64_t N, int64_t lda, 
 rd_status rd_power_slot(int64_t N, int64_t lda, int kmax, size_t work_bytes, int k, size_t *byte_offset);
 
 /*
+ * rd_power_until_periodic_noalloc -- the same search as rd_power_until_periodic
+ * (same arguments and results, minus the work buffer), for callers that must not
+ * allocate device memory: for example code whose device memory is all owned by
+ * another allocator (a framework's caching pool, where a cudaMalloc would fail or
+ * fragment it), plug-ins whose host forbids device allocations, and
+ * latency-critical loops that cannot afford cudaMalloc/cudaFree, which may
+ * synchronise the whole device.  The paper has no counterpart; this is a
+ * deployment convenience.
+ *   Scratch: a static device array of RD_NOALLOC_SCRATCH_BYTES inside the
+ *   library (its own module: reserved on a device once this entry point is first
+ *   used there, and held until the process exits).  Problems that need more --
+ *   rd_power_work_bytes(N, lda, kmax, 2) > RD_NOALLOC_SCRATCH_BYTES -- are
+ *   rejected with RD_ERR_NOMEM before any device work; within the limit the ring
+ *   holds as many powers as fit (A(G) for m <= 7: 7 powers of N = 2507).
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call before
+ *   any stream capture begins.
+ *   Sharing: every call on a device uses the same array, which keeps the previous
+ *   call's contents; each call re-initialises the state it reads, so no clearing
+ *   is needed between calls.  Calls that overlap on the GPU (two host threads,
+ *   two streams of one device) race on the array; the call synchronises its
+ *   stream before returning, so calls made one after another never overlap.
+ * Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+#define RD_NOALLOC_SCRATCH_BYTES (96u * 1024u * 1024u)
+rd_status rd_power_until_periodic_noalloc(const int16_t *A_dev, int64_t N, int64_t lda, int kmax,
+                                          int64_t *gamma_host, int32_t *k_out, int32_t *p_out, int64_t *q_out,
+                                          cudaStream_t s);
+
+/*
  * rd_gamma_R -- gamma_R(P_m box C_n) for m in [1, RD_MAX_M], n >= 3 (C_n needs
  * n >= 3).  The first call for a given m builds A(G) and runs
  * rd_power_until_periodic on the current device, in device memory this call

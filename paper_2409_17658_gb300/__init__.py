@@ -58,9 +58,10 @@ def _lib():
         lib.rd_power_until_periodic.argtypes = [vp, i64, i64, ctypes.c_int, vp, sz, vp, vp, vp, vp, vp]
         lib.rd_gamma_R.argtypes = [ctypes.c_int, i64, vp]
         lib.rd_power_slot.argtypes = [i64, i64, ctypes.c_int, sz, ctypes.c_int, vp]
+        lib.rd_power_until_periodic_noalloc.argtypes = [vp, i64, i64, ctypes.c_int, vp, vp, vp, vp, vp]
         for name in ("rd_state_count", "rd_padded_dim", "rd_enumerate_states", "rd_build_transfer",
                      "rd_minplus_gemm", "rd_power_work_bytes", "rd_power_until_periodic", "rd_gamma_R",
-                     "rd_power_slot"):
+                     "rd_power_slot", "rd_power_until_periodic_noalloc"):
             getattr(lib, name).restype = st
         _ = i32
         _LIB = lib
@@ -147,6 +148,19 @@ def power_until_periodic(A, n: int, kmax: int, work, stream=None) -> dict:
                                         ctypes.c_void_p(gamma.ctypes.data), ctypes.byref(k), ctypes.byref(p),
                                         ctypes.byref(q), _stream(stream))
     _check(st, "rd_power_until_periodic", ok=(RD_OK, RD_NOT_FOUND))
+    found = st == RD_OK
+    j = k.value + p.value if found else kmax
+    return dict(status=st, found=found, k=k.value if found else None, p=p.value if found else None,
+                q=q.value if found else None, j=j, gamma=gamma)
+
+
+def power_until_periodic_noalloc(A, n: int, kmax: int, stream=None) -> dict:
+    """rd_power_until_periodic on the library's static scratch (no work buffer, no allocation)."""
+    gamma = np.zeros(kmax + 1, dtype=np.int64)
+    k, p, q = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    st = _lib().rd_power_until_periodic_noalloc(_dptr(A), n, A.stride(0), kmax, ctypes.c_void_p(gamma.ctypes.data),
+                                                ctypes.byref(k), ctypes.byref(p), ctypes.byref(q), _stream(stream))
+    _check(st, "rd_power_until_periodic_noalloc", ok=(RD_OK, RD_NOT_FOUND))
     found = st == RD_OK
     j = k.value + p.value if found else kmax
     return dict(status=st, found=found, k=k.value if found else None, p=p.value if found else None,

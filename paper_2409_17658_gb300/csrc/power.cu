@@ -309,6 +309,62 @@ rd_status fail(cudaError_t e) {
 }
 
 }  // namespace
+
+// The same run as rd_power_until_periodic, on a work area the caller has already
+// validated, with no host heap use: the gamma table is copied straight into
+// gamma_host.  Serves the no-allocation entry point.
+rd_status power_run_without_heap(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, void* work_dev,
+                                 size_t work_bytes, int64_t* gamma_host, int32_t* k_out, int32_t* p_out,
+                                 int64_t* q_out, cudaStream_t s) {
+  const size_t sb = state_bytes(kmax), pb = slot_bytes(N, lda);
+  if (work_bytes < sb + 2 * pb) return RD_ERR_NOMEM;
+  const size_t slots64 = (work_bytes - sb) / pb;
+  Run r{};
+  r.st = reinterpret_cast<PowerState*>(work_dev);
+  r.ring = reinterpret_cast<int16_t*>(reinterpret_cast<char*>(work_dev) + sb);
+  r.slot_elems = (int64_t)(pb / 2);
+  r.slots = (int)(slots64 > (size_t)kmax + 1 ? (size_t)kmax + 1 : slots64);
+  r.N = N;
+  r.ld = lda;
+  r.A = A_dev;
+  r.grid = reduction_grid();
+  cudaError_t e = enqueue_first(r, kmax, s);
+  if (e != cudaSuccess) return fail(e);
+  const int chunk = (N >= 2048) ? 1 : (N >= 512 ? 4 : 16);
+  int enqueued = 1;
+  PowerState h{};
+  for (;;) {
+    e = cudaMemcpyAsync(&h, r.st, sizeof(PowerState), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(e);
+    if (h.done || enqueued >= kmax) break;
+    const int n = (kmax - enqueued < chunk) ? (kmax - enqueued) : chunk;
+    for (int i = 0; i < n; ++i) {
+      e = enqueue_step(r, s);
+      if (e != cudaSuccess) return fail(e);
+    }
+    enqueued += n;
+  }
+  const int last = (h.done == 1) ? h.found_j : h.k;
+  e = cudaMemcpyAsync(gamma_host, reinterpret_cast<char*>(work_dev) + kStateHeader + 8 * (size_t)(kmax + 1),
+                      8 * (size_t)(kmax + 1), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(e);
+  for (int k = 0; k <= kmax; ++k)
+    if (k < 1 || k > last) gamma_host[k] = RD_GAMMA_UNSET;
+  if (h.done == 1) {
+    *k_out = h.found_i;
+    *p_out = h.found_j - h.found_i;
+    *q_out = h.found_q;
+    return RD_OK;
+  }
+  *k_out = 0;
+  *p_out = 0;
+  *q_out = 0;
+  if (h.done == 3) return (h.err & 1) ? RD_ERR_RANGE : RD_ERR_NOMEM;
+  return RD_NOT_FOUND;
+}
+
 }  // namespace rd
 
 using namespace rd;

@@ -74,6 +74,10 @@ struct GemmParams {
 cudaError_t launch_minplus_gemm(const GemmParams& p, bool ring, cudaStream_t s);
 cudaError_t launch_fill_i32(int32_t* dst, int32_t value, cudaStream_t s);
 
+rd_status power_run_without_heap(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, void* work_dev,
+                                 size_t work_bytes, int64_t* gamma_host, int32_t* k_out, int32_t* p_out,
+                                 int64_t* q_out, cudaStream_t s);
+
 void set_cuda_error(cudaError_t e);
 bool aligned16(const void* p);
 
