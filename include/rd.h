@@ -143,6 +143,66 @@ rd_status rd_power_until_periodic(const int16_t *A_dev, int64_t N, int64_t lda, 
 rd_status rd_power_slot(int64_t N, int64_t lda, int kmax, size_t work_bytes, int k, size_t *byte_offset);
 
 /*
+ * Dense x sparse power step (the left operand sparse).  A(G) has few finite
+ * entries (0.55 % at m = 9) while its powers are dense; since A^k (x) A =
+ * A (x) A^k, a power step can be R = A (x) P_k, whose row i is the entrywise
+ * minimum over the arcs i -> t of A[i][t] + row t of P_k: N nnz(A) add-mins
+ * instead of N^3 (Theorem 1: extend every walk by one arc).
+ *
+ * Block-sparse form of an M x K operand A: rows in blocks of R consecutive rows
+ * (R in {1, 2, 4, 8}); for block b, entries block_start[b] .. block_start[b+1]-1
+ * list, in increasing order, the columns t (entry_col) where some row of the
+ * block is finite, and entry_w[e*R + r] holds A[b*R + r][t] in both halfwords
+ * (RD_INF when that row has no arc to t).  All three arrays are device memory
+ * owned by the caller: block_start has ceil(M/R) + 1 int64, entry_col has
+ * `entries` uint32 and entry_w has entries * R uint32.
+ *
+ * rd_sparse_count -- fills block_start (exclusive prefix sums of the per-block
+ * entry counts; block_start[ceil(M/R)] = total) and returns the total in
+ * *entries_host.  Synchronises the stream.
+ */
+rd_status rd_sparse_count(const int16_t *A, int64_t lda, int64_t M, int64_t K, int R, int64_t *block_start_dev,
+                          int64_t *entries_host, cudaStream_t s);
+
+/* rd_sparse_build -- fills entry_col and entry_w from A and the block_start of rd_sparse_count. */
+rd_status rd_sparse_build(const int16_t *A, int64_t lda, int64_t M, int64_t K, int R, const int64_t *block_start_dev,
+                          uint32_t *entry_col_dev, uint32_t *entry_w_dev, cudaStream_t s);
+
+/*
+ * rd_sparse_minplus -- C = A (x) B (Sec. 3) with A (M x K) in block-sparse form
+ * and B a dense K x N matrix (ldb), C dense M x N (ldc); same conventions and
+ * min_out as rd_minplus_gemm.  C may not alias B.
+ */
+rd_status rd_sparse_minplus(int R, int64_t M, const int64_t *block_start, const uint32_t *entry_col,
+                            const uint32_t *entry_w, const int16_t *B, int64_t ldb, int64_t N, int16_t *C, int64_t ldc,
+                            int32_t *min_out, cudaStream_t s);
+
+/*
+ * rd_power_until_periodic_sparse -- rd_power_until_periodic (same work buffer,
+ * outputs and errors) with the power step R = A (x) P_k on the block-sparse form
+ * of the same A (built from A_dev with rd_sparse_count / rd_sparse_build).
+ * A_dev is still read once, for the first power.
+ */
+rd_status rd_power_until_periodic_sparse(const int16_t *A_dev, int64_t N, int64_t lda, int R,
+                                         const int64_t *block_start, const uint32_t *entry_col,
+                                         const uint32_t *entry_w, int kmax, void *work_dev, size_t work_bytes,
+                                         int64_t *gamma_host, int32_t *k_out, int32_t *p_out, int64_t *q_out,
+                                         cudaStream_t s);
+
+/*
+ * rd_sparse_tune -- autotuner for the rows per block R of the sparse step: for
+ * R = 1, 2, 4, 8 it builds the block-sparse form of the N x N operand A in
+ * scratch_dev, times three products A (x) A (the same bytes and DPX work as a
+ * power step) with CUDA events, and returns the fastest R in *best_R;
+ * ms_per_R[0..3] (nullable) receives the times (-1 for a candidate whose plan
+ * did not fit).  scratch_dev (256-byte aligned) must hold an N x lda int16
+ * result plus the plans; a power work buffer's ring is large enough.
+ * Synchronous.
+ */
+rd_status rd_sparse_tune(const int16_t *A, int64_t lda, int64_t N, void *scratch_dev, size_t scratch_bytes,
+                         int *best_R, float *ms_per_R, cudaStream_t s);
+
+/*
  * rd_power_until_periodic_noalloc -- the same search as rd_power_until_periodic
  * (same arguments and results, minus the work buffer), for callers that must not
  * allocate device memory: for example code whose device memory is all owned by
@@ -175,8 +235,9 @@ rd_status rd_power_until_periodic_noalloc(const int16_t *A_dev, int64_t N, int64
 /*
  * rd_gamma_R -- gamma_R(P_m box C_n) for m in [1, RD_MAX_M], n >= 3 (C_n needs
  * n >= 3).  The first call for a given m builds A(G) and runs
- * rd_power_until_periodic on the current device, in device memory this call
- * allocates and frees; the result (gamma for n < k + p, and (k, p, q)) is
+ * rd_power_until_periodic_sparse (R = 2) on the current device, in device
+ * memory this call allocates and frees (about 9 powers of C_m x C_m int16: 8 GB
+ * at m = 9, 76 GB at m = 10; RD_ERR_NOMEM when that does not fit); the result (gamma for n < k + p, and (k, p, q)) is
  * cached per m for the life of the process, and later calls evaluate the
  * solution of the finite-difference equation of Prop. 7 on the host:
  * gamma(n) = gamma(k + (n - k) mod p) + q floor((n - k) / p) for n >= k.

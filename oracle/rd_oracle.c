@@ -321,6 +321,40 @@ int rdo_power_until_periodic(int m, const int64_t *A_in, int64_t N_in, int kmax,
 }
 
 /*
+ * Arc lists of A(G) straight from the follow rules (Cor. 6), without the dense
+ * matrix: arcs q -> p with label wt[p], p in increasing order.
+ */
+static int build_arcs_from_rules(int m, int64_t N, const uint32_t *code, const int32_t *wt, int64_t **ptr,
+                                 int64_t **col, int64_t **w) {
+  *ptr = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N + 1));
+  if (!*ptr) return 2;
+  int64_t *deg = *ptr + 1;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t q = 0; q < N; ++q) {
+    int64_t d = 0;
+    for (int64_t p = 0; p < N; ++p) d += rdo_follows(m, code[q], code[p]);
+    deg[q] = d;
+  }
+  (*ptr)[0] = 0;
+  for (int64_t q = 0; q < N; ++q) (*ptr)[q + 1] += (*ptr)[q];
+  const int64_t nnz = (*ptr)[N];
+  *col = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nnz ? nnz : 1));
+  *w = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nnz ? nnz : 1));
+  if (!*col || !*w) return 2;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t q = 0; q < N; ++q) {
+    int64_t e = (*ptr)[q];
+    for (int64_t p = 0; p < N; ++p)
+      if (rdo_follows(m, code[q], code[p])) {
+        (*col)[e] = p;
+        (*w)[e] = wt[p];
+        ++e;
+      }
+  }
+  return 0;
+}
+
+/*
  * Selected rows of the raw powers: out[(k-1)*nrows*N + r*N + j] = (A^k)[rows[r]][j]
  * for k = 1..kmax, by repeated vector-matrix products e_i (x) A (x) A ...
  * (Theorem 1 applied to walks starting at one word).  Infinity is RDO_INF.
@@ -328,15 +362,17 @@ int rdo_power_until_periodic(int m, const int64_t *A_in, int64_t N_in, int kmax,
 int rdo_power_rows(int m, const int64_t *rows, int nrows, int kmax, int64_t *out) {
   int64_t N = rdo_num_words(m);
   if (N <= 0 || kmax < 1) return 1;
-  int64_t *A = (int64_t *)malloc(sizeof(int64_t) * (size_t)N * (size_t)N);
-  if (!A) return 2;
-  rdo_transfer(m, A, N);
+  uint32_t *code = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N);
+  int32_t *wt = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+  if (!code || !wt) { free(code); free(wt); return 2; }
+  rdo_words(m, code, wt, N);
   int64_t *ptr = 0, *col = 0, *w = 0;
-  if (build_arcs(A, N, &ptr, &col, &w)) { free(A); return 2; }
+  if (build_arcs_from_rules(m, N, code, wt, &ptr, &col, &w)) { free(code); free(wt); free(ptr); free(col); free(w); return 2; }
 #pragma omp parallel for schedule(dynamic, 1)
   for (int r = 0; r < nrows; ++r) {
-    int64_t *cur = out + (size_t)r * N; /* k = 1 */
-    for (int64_t j = 0; j < N; ++j) cur[j] = A[rows[r] * N + j];
+    int64_t *cur = out + (size_t)r * N; /* k = 1: row rows[r] of A */
+    for (int64_t j = 0; j < N; ++j) cur[j] = RDO_INF;
+    for (int64_t e = ptr[rows[r]]; e < ptr[rows[r] + 1]; ++e) cur[col[e]] = w[e];
     for (int k = 2; k <= kmax; ++k) {
       int64_t *prev = out + ((size_t)(k - 2) * nrows + r) * N;
       int64_t *nxt = out + ((size_t)(k - 1) * nrows + r) * N;
@@ -350,7 +386,7 @@ int rdo_power_rows(int m, const int64_t *rows, int nrows, int kmax, int64_t *out
       }
     }
   }
-  free(A); free(ptr); free(col); free(w);
+  free(code); free(wt); free(ptr); free(col); free(w);
   return 0;
 }
 

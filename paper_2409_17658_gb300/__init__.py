@@ -59,9 +59,16 @@ def _lib():
         lib.rd_gamma_R.argtypes = [ctypes.c_int, i64, vp]
         lib.rd_power_slot.argtypes = [i64, i64, ctypes.c_int, sz, ctypes.c_int, vp]
         lib.rd_power_until_periodic_noalloc.argtypes = [vp, i64, i64, ctypes.c_int, vp, vp, vp, vp, vp]
+        lib.rd_sparse_count.argtypes = [vp, i64, i64, i64, ctypes.c_int, vp, vp, vp]
+        lib.rd_sparse_build.argtypes = [vp, i64, i64, i64, ctypes.c_int, vp, vp, vp, vp]
+        lib.rd_sparse_minplus.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, i64, i64, vp, i64, vp, vp]
+        lib.rd_sparse_tune.argtypes = [vp, i64, i64, vp, sz, vp, vp, vp]
+        lib.rd_power_until_periodic_sparse.argtypes = [vp, i64, i64, ctypes.c_int, vp, vp, vp, ctypes.c_int, vp, sz,
+                                                       vp, vp, vp, vp, vp]
         for name in ("rd_state_count", "rd_padded_dim", "rd_enumerate_states", "rd_build_transfer",
                      "rd_minplus_gemm", "rd_power_work_bytes", "rd_power_until_periodic", "rd_gamma_R",
-                     "rd_power_slot", "rd_power_until_periodic_noalloc"):
+                     "rd_power_slot", "rd_power_until_periodic_noalloc", "rd_sparse_count", "rd_sparse_build",
+                     "rd_sparse_minplus", "rd_power_until_periodic_sparse", "rd_sparse_tune"):
             getattr(lib, name).restype = st
         _ = i32
         _LIB = lib
@@ -161,6 +168,66 @@ def power_until_periodic_noalloc(A, n: int, kmax: int, stream=None) -> dict:
     st = _lib().rd_power_until_periodic_noalloc(_dptr(A), n, A.stride(0), kmax, ctypes.c_void_p(gamma.ctypes.data),
                                                 ctypes.byref(k), ctypes.byref(p), ctypes.byref(q), _stream(stream))
     _check(st, "rd_power_until_periodic_noalloc", ok=(RD_OK, RD_NOT_FOUND))
+    found = st == RD_OK
+    j = k.value + p.value if found else kmax
+    return dict(status=st, found=found, k=k.value if found else None, p=p.value if found else None,
+                q=q.value if found else None, j=j, gamma=gamma)
+
+
+def sparse_count(A, M: int, K: int, R: int, block_start, stream=None) -> int:
+    """Block-sparse form, step 1: block_start (int64, ceil(M/R)+1) and the number of entries."""
+    ent = ctypes.c_int64()
+    _check(_lib().rd_sparse_count(_dptr(A), A.stride(0), M, K, R, _dptr(block_start), ctypes.byref(ent),
+                                  _stream(stream)), "rd_sparse_count")
+    return ent.value
+
+
+def sparse_build(A, M: int, K: int, R: int, block_start, entry_col, entry_w, stream=None) -> None:
+    """Block-sparse form, step 2: entry_col (int32 view of uint32) and entry_w (duplicated weights)."""
+    _check(_lib().rd_sparse_build(_dptr(A), A.stride(0), M, K, R, _dptr(block_start), _dptr(entry_col),
+                                  _dptr(entry_w), _stream(stream)), "rd_sparse_build")
+
+
+def sparse_plan(A, M: int, K: int, R: int = 4, stream=None) -> dict:
+    """Allocate (torch) and build the block-sparse form of A[:M, :K]."""
+    import torch
+
+    nb = (M + R - 1) // R
+    start = torch.empty(nb + 1, dtype=torch.int64, device=A.device)
+    ent = sparse_count(A, M, K, R, start, stream)
+    col = torch.empty(max(ent, 1), dtype=torch.int32, device=A.device)
+    w = torch.empty(max(ent, 1) * R, dtype=torch.int32, device=A.device)
+    sparse_build(A, M, K, R, start, col, w, stream)
+    return dict(R=R, M=M, K=K, entries=ent, block_start=start, entry_col=col, entry_w=w)
+
+
+def sparse_minplus(plan: dict, B, C, N: int | None = None, min_out=None, stream=None) -> None:
+    """C[:M, :N] = A (x) B[:K, :N] with A given by sparse_plan()."""
+    N = C.shape[1] if N is None else N
+    mo = _dptr(min_out) if min_out is not None else None
+    _check(_lib().rd_sparse_minplus(plan["R"], plan["M"], _dptr(plan["block_start"]), _dptr(plan["entry_col"]),
+                                    _dptr(plan["entry_w"]), _dptr(B), B.stride(0), N, _dptr(C), C.stride(0), mo,
+                                    _stream(stream)), "rd_sparse_minplus")
+
+
+def sparse_tune(A, n: int, scratch, stream=None):
+    """Native autotuner: (best R, {R: ms per product A (x) A}) for the sparse step on A[:n, :n]."""
+    best = ctypes.c_int()
+    ms = (ctypes.c_float * 4)()
+    _check(_lib().rd_sparse_tune(_dptr(A), A.stride(0), n, _dptr(scratch), scratch.numel() * scratch.element_size(),
+                                 ctypes.byref(best), ms, _stream(stream)), "rd_sparse_tune")
+    return best.value, {R: ms[i] for i, R in enumerate((1, 2, 4, 8)) if ms[i] >= 0}
+
+
+def power_until_periodic_sparse(A, n: int, plan: dict, kmax: int, work, stream=None) -> dict:
+    """rd_power_until_periodic with the dense x sparse step."""
+    gamma = np.zeros(kmax + 1, dtype=np.int64)
+    k, p, q = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    st = _lib().rd_power_until_periodic_sparse(_dptr(A), n, A.stride(0), plan["R"], _dptr(plan["block_start"]),
+                                               _dptr(plan["entry_col"]), _dptr(plan["entry_w"]), kmax, _dptr(work),
+                                               work.numel() * work.element_size(), ctypes.c_void_p(gamma.ctypes.data),
+                                               ctypes.byref(k), ctypes.byref(p), ctypes.byref(q), _stream(stream))
+    _check(st, "rd_power_until_periodic_sparse", ok=(RD_OK, RD_NOT_FOUND))
     found = st == RD_OK
     j = k.value + p.value if found else kmax
     return dict(status=st, found=found, k=k.value if found else None, p=p.value if found else None,

@@ -258,16 +258,6 @@ int reduction_grid() {
   return sms * 4;
 }
 
-struct Run {
-  PowerState* st;
-  int16_t* ring;
-  int64_t slot_elems;
-  int slots;
-  int64_t N, ld;
-  const int16_t* A;
-  int grid;
-};
-
 cudaError_t enqueue_first(const Run& r, int kmax, cudaStream_t s) {
   init_state_kernel<<<1, 256, 0, s>>>(r.st, kmax, r.slots);
   reduce_min_diag_kernel<<<r.grid, kRedThreads, 0, s>>>(r.A, r.N, r.ld, r.st);
@@ -277,24 +267,9 @@ cudaError_t enqueue_first(const Run& r, int kmax, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t enqueue_step(const Run& r, cudaStream_t s) {
-  GemmParams p{};
-  p.A = nullptr;
-  p.lda = r.ld;
-  p.B = r.A;
-  p.ldb = r.ld;
-  p.C = nullptr;
-  p.ldc = r.ld;
-  p.M = r.N;
-  p.N = r.N;
-  p.K = r.N;
-  p.min_out = &r.st->mu;
-  p.diag_out = &r.st->dmin;
-  p.st = r.st;
-  p.ring = r.ring;
-  p.slot_elems = r.slot_elems;
-  p.slots = r.slots;
-  cudaError_t e = launch_minplus_gemm(p, true, s);
+// One power step: the product (dense or sparse), then normalise/hash, finalize, compare.
+cudaError_t enqueue_step(const Run& r, ProductFn product, const void* ctx, cudaStream_t s) {
+  cudaError_t e = product(r, ctx, s);
   if (e != cudaSuccess) return e;
   normalise_hash_kernel<false><<<r.grid, kRedThreads, 0, s>>>(nullptr, r.st, r.ring, r.slot_elems, r.slots, r.N,
                                                                r.ld);
@@ -310,12 +285,30 @@ rd_status fail(cudaError_t e) {
 
 }  // namespace
 
-// The same run as rd_power_until_periodic, on a work area the caller has already
-// validated, with no host heap use: the gamma table is copied straight into
-// gamma_host.  Serves the no-allocation entry point.
-rd_status power_run_without_heap(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, void* work_dev,
-                                 size_t work_bytes, int64_t* gamma_host, int32_t* k_out, int32_t* p_out,
-                                 int64_t* q_out, cudaStream_t s) {
+// R = P_k (x) A with the DPX GEMM in ring mode.
+cudaError_t dense_power_product(const Run& r, const void*, cudaStream_t s) {
+  GemmParams p{};
+  p.lda = r.ld;
+  p.B = r.A;
+  p.ldb = r.ld;
+  p.ldc = r.ld;
+  p.M = r.N;
+  p.N = r.N;
+  p.K = r.N;
+  p.min_out = &r.st->mu;
+  p.diag_out = &r.st->dmin;
+  p.st = r.st;
+  p.ring = r.ring;
+  p.slot_elems = r.slot_elems;
+  p.slots = r.slots;
+  return launch_minplus_gemm(p, true, s);
+}
+
+// Algorithm 2 on a validated work area: state header, then the ring of powers.
+// No host heap use: the gamma table is copied straight into gamma_host.
+rd_status power_search(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, void* work_dev, size_t work_bytes,
+                       ProductFn product, const void* ctx, int64_t* gamma_host, int32_t* k_out, int32_t* p_out,
+                       int64_t* q_out, cudaStream_t s) {
   const size_t sb = state_bytes(kmax), pb = slot_bytes(N, lda);
   if (work_bytes < sb + 2 * pb) return RD_ERR_NOMEM;
   const size_t slots64 = (work_bytes - sb) / pb;
@@ -330,6 +323,8 @@ rd_status power_run_without_heap(const int16_t* A_dev, int64_t N, int64_t lda, i
   r.grid = reduction_grid();
   cudaError_t e = enqueue_first(r, kmax, s);
   if (e != cudaSuccess) return fail(e);
+  // Steps per host check: large products are long enough that one check per
+  // step costs nothing; small ones are batched (surplus steps exit at once).
   const int chunk = (N >= 2048) ? 1 : (N >= 512 ? 4 : 16);
   int enqueued = 1;
   PowerState h{};
@@ -340,7 +335,7 @@ rd_status power_run_without_heap(const int16_t* A_dev, int64_t N, int64_t lda, i
     if (h.done || enqueued >= kmax) break;
     const int n = (kmax - enqueued < chunk) ? (kmax - enqueued) : chunk;
     for (int i = 0; i < n; ++i) {
-      e = enqueue_step(r, s);
+      e = enqueue_step(r, product, ctx, s);
       if (e != cudaSuccess) return fail(e);
     }
     enqueued += n;
@@ -391,58 +386,8 @@ extern "C" rd_status rd_power_until_periodic(const int16_t* A_dev, int64_t N, in
   if (!A_dev || !work_dev || !gamma_host || !k_out || !p_out || !q_out) return RD_ERR_ARG;
   if (N < 1 || lda < N || lda % 8 != 0 || kmax < 1 || kmax > (1 << 20)) return RD_ERR_ARG;
   if (!aligned16(A_dev) || (reinterpret_cast<uintptr_t>(work_dev) & 255u) != 0) return RD_ERR_ARG;
-  const size_t sb = state_bytes(kmax), pb = slot_bytes(N, lda);
-  if (work_bytes < sb + 2 * pb) return RD_ERR_NOMEM;
-  const size_t slots64 = (work_bytes - sb) / pb;
-  Run r{};
-  r.st = reinterpret_cast<PowerState*>(work_dev);
-  r.ring = reinterpret_cast<int16_t*>(reinterpret_cast<char*>(work_dev) + sb);
-  r.slot_elems = (int64_t)(pb / 2);
-  r.slots = (int)(slots64 > (size_t)kmax + 1 ? (size_t)kmax + 1 : slots64);
-  r.N = N;
-  r.ld = lda;
-  r.A = A_dev;
-  r.grid = reduction_grid();
-
-  cudaError_t e = enqueue_first(r, kmax, s);
-  if (e != cudaSuccess) return fail(e);
-  // Steps per host check: large products are long enough that one check per
-  // step costs nothing; small ones are batched (surplus steps exit at once).
-  const int chunk = (N >= 2048) ? 1 : (N >= 512 ? 4 : 16);
-  int enqueued = 1;
-  PowerState h{};
-  for (;;) {
-    e = cudaMemcpyAsync(&h, r.st, sizeof(PowerState), cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return fail(e);
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return fail(e);
-    if (h.done || enqueued >= kmax) break;
-    const int n = (kmax - enqueued < chunk) ? (kmax - enqueued) : chunk;
-    for (int i = 0; i < n; ++i) {
-      e = enqueue_step(r, s);
-      if (e != cudaSuccess) return fail(e);
-    }
-    enqueued += n;
-  }
-  std::vector<int64_t> g((size_t)kmax + 1);
-  e = cudaMemcpyAsync(g.data(), reinterpret_cast<char*>(work_dev) + kStateHeader + 8 * (size_t)(kmax + 1),
-                      8 * (size_t)(kmax + 1), cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return fail(e);
-  e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return fail(e);
-  const int last = (h.done == 1) ? h.found_j : h.k;
-  for (int k = 0; k <= kmax; ++k) gamma_host[k] = (k >= 1 && k <= last) ? g[(size_t)k] : RD_GAMMA_UNSET;
-  if (h.done == 1) {
-    *k_out = h.found_i;
-    *p_out = h.found_j - h.found_i;
-    *q_out = h.found_q;
-    return RD_OK;
-  }
-  *k_out = 0;
-  *p_out = 0;
-  *q_out = 0;
-  if (h.done == 3) return (h.err & 1) ? RD_ERR_RANGE : RD_ERR_NOMEM;
-  return RD_NOT_FOUND;
+  return power_search(A_dev, N, lda, kmax, work_dev, work_bytes, dense_power_product, nullptr, gamma_host, k_out,
+                      p_out, q_out, s);
 }
 
 // ---------------------------------------------------------------- rd_gamma_R: per-process cache
@@ -481,7 +426,43 @@ rd_status compute_cached(int m, Cached* out) {
     rc = (e == cudaErrorMemoryAllocation) ? RD_ERR_NOMEM : RD_ERR_CUDA;
   }
   if (rc == RD_OK) rc = rd_build_transfer(m, A, ld, s);
-  if (rc == RD_OK) rc = rd_power_until_periodic(A, N, ld, kGammaKmax, work, wbytes, g.data(), &k, &p, &q, s);
+  // the dense x sparse step (A(G) is sparse, its powers are dense)
+  int kR = 2;
+  if (rc == RD_OK && N >= 1024) {  // small matrices: any R is a few microseconds
+    int best = 0;
+    const size_t sb = state_bytes(kGammaKmax);
+    rc = rd_sparse_tune(A, ld, N, static_cast<char*>(work) + sb, wbytes - sb, &best, nullptr, s);
+    if (rc == RD_OK) kR = best;
+  }
+  const int64_t nb = (N + kR - 1) / kR;
+  int64_t* start = nullptr;
+  uint32_t* ecol = nullptr;
+  uint32_t* ew = nullptr;
+  int64_t entries = 0;
+  if (rc == RD_OK) {
+    e = cudaMalloc(&start, (size_t)(nb + 1) * sizeof(int64_t));
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      rc = (e == cudaErrorMemoryAllocation) ? RD_ERR_NOMEM : RD_ERR_CUDA;
+    }
+  }
+  if (rc == RD_OK) rc = rd_sparse_count(A, ld, N, N, kR, start, &entries, s);
+  if (rc == RD_OK) {
+    e = cudaMalloc(&ecol, (size_t)(entries > 0 ? entries : 1) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&ew, (size_t)(entries > 0 ? entries : 1) * 4 * kR);
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      rc = (e == cudaErrorMemoryAllocation) ? RD_ERR_NOMEM : RD_ERR_CUDA;
+    }
+  }
+  if (rc == RD_OK) rc = rd_sparse_build(A, ld, N, N, kR, start, ecol, ew, s);
+  if (rc == RD_OK)
+    rc = rd_power_until_periodic_sparse(A, N, ld, kR, start, ecol, ew, kGammaKmax, work, wbytes, g.data(), &k, &p,
+                                        &q, s);
+  if (s) cudaStreamSynchronize(s);
+  if (start) cudaFree(start);
+  if (ecol) cudaFree(ecol);
+  if (ew) cudaFree(ew);
   if (A) cudaFree(A);
   if (work) cudaFree(work);
   if (s) cudaStreamDestroy(s);

@@ -74,9 +74,26 @@ struct GemmParams {
 cudaError_t launch_minplus_gemm(const GemmParams& p, bool ring, cudaStream_t s);
 cudaError_t launch_fill_i32(int32_t* dst, int32_t value, cudaStream_t s);
 
-rd_status power_run_without_heap(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, void* work_dev,
-                                 size_t work_bytes, int64_t* gamma_host, int32_t* k_out, int32_t* p_out,
-                                 int64_t* q_out, cudaStream_t s);
+// One run of the period search (power.cu): the device state, the ring of powers and the operand.
+struct Run {
+  PowerState* st;
+  int16_t* ring;
+  int64_t slot_elems;
+  int slots;
+  int64_t N, ld;
+  const int16_t* A;
+  int grid;
+};
+
+// Enqueues R = (next raw power) into the ring slot of power st->k + 1, with min and diag-min into
+// st->mu and st->dmin.  `ctx` carries the product's own operands.
+typedef cudaError_t (*ProductFn)(const Run& r, const void* ctx, cudaStream_t s);
+
+cudaError_t dense_power_product(const Run& r, const void* ctx, cudaStream_t s);
+
+rd_status power_search(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, void* work_dev, size_t work_bytes,
+                       ProductFn product, const void* ctx, int64_t* gamma_host, int32_t* k_out, int32_t* p_out,
+                       int64_t* q_out, cudaStream_t s);
 
 void set_cuda_error(cudaError_t e);
 bool aligned16(const void* p);

@@ -285,3 +285,115 @@ def test_gamma_R_closed_forms_m7(rd):
     for n in range(3, 120):
         want = 20 if n == 6 else math.ceil(16 * n / 5) + (0 if n % 5 == 0 else 1)
         assert rd.gamma_R(7, n) == want, n
+
+
+# ---------------------------------------------------------------- f1: dense x sparse step
+
+SPARSE_SHAPES = [(1, 1, 1), (5, 9, 13), (33, 33, 33), (37, 300, 1000), (130, 200, 1030), (257, 640, 2049)]
+
+
+@pytest.mark.parametrize("R", [1, 2, 4, 8])
+@pytest.mark.parametrize("shape", SPARSE_SHAPES)
+def test_sparse_minplus(rd, torch_mod, orc, shape, R):
+    torch = torch_mod
+    from paper_2409_17658_gb300 import inputs
+
+    M, K, N = shape
+    a = inputs.matrix(M, K, seed=41, dist="wide")
+    keep = inputs.matrix(M, K, seed=43, dist="u32") < 3  # about 5 % of the entries stay finite
+    a = np.where(keep, a, I16_INF).astype(np.int16)
+    b = inputs.matrix(K, N, seed=42, dist="wide")
+    A = upload(torch, a, junk=-5)
+    B = upload(torch, b, junk=-5)
+    plan = rd.sparse_plan(A, M, K, R)
+    # the plan lists, per block of R rows, the union of finite columns
+    fin = a != I16_INF
+    want_entries = sum(int(fin[i0:i0 + R].any(0).sum()) for i0 in range(0, M, R))
+    assert plan["entries"] == want_entries
+    C = torch.full((M, (N + 7) // 8 * 8), 777, dtype=torch.int16, device="cuda")
+    mn = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rd.sparse_minplus(plan, B, C, N, min_out=mn)
+    want = orc.minplus_i16(a, b)
+    got = C.cpu().numpy()
+    assert np.array_equal(got[:, :N].astype(np.int32), want)
+    assert np.all(got[:, N:] == 777)
+    assert mn.item() == want.min()
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_power_sparse_matches_oracle(rd, torch_mod, orc, m):
+    A, n = rd.transfer_matrix(m)
+    plan = rd.sparse_plan(A, n, n, 4)
+    work = rd.power_workspace(n, A.stride(0), 40, 8)
+    r = rd.power_until_periodic_sparse(A, n, plan, 40, work)
+    o = orc.power_until_periodic(m, kmax=40)
+    assert (r["k"], r["p"], r["q"]) == (o["k"], o["p"], o["q"])
+    assert np.array_equal(r["gamma"][1:r["j"] + 1], o["gamma"][1:o["j"] + 1])
+
+
+@pytest.mark.parametrize("R", [1, 2, 8])
+def test_power_sparse_m9_equals_dense(rd, torch_mod, orc, R):
+    A, n = rd.transfer_matrix(9)
+    plan = rd.sparse_plan(A, n, n, R)
+    work = rd.power_workspace(n, A.stride(0), 40, 8)
+    r = rd.power_until_periodic_sparse(A, n, plan, 40, work)
+    assert (r["k"], r["p"], r["q"]) == (22, 5, 20)
+    for nn in range(3, 8):
+        assert r["gamma"][nn] == orc.row_dp(9, nn)
+    # same gamma sequence as the dense step
+    work2 = rd.power_workspace(n, A.stride(0), 40, 8)
+    d = rd.power_until_periodic(A, n, 40, work2)
+    assert np.array_equal(r["gamma"], d["gamma"])
+    # the resident final power agrees with the dense run bit for bit
+    off = rd.power_slot(n, A.stride(0), 40, work.numel(), r["j"])
+    off2 = rd.power_slot(n, A.stride(0), 40, work2.numel(), d["j"])
+    ld = A.stride(0)
+    assert torch_mod.equal(work[off:off + n * ld * 2].view(torch_mod.int16).view(n, ld)[:, :n],
+                           work2[off2:off2 + n * ld * 2].view(torch_mod.int16).view(n, ld)[:, :n])
+
+
+# ---------------------------------------------------------------- f3: m = 10 (N = 64769)
+
+def test_power_m10(rd, torch_mod, orc):
+    """m = 10 has no Table 2 row.  What the paper fixes: gamma = 22n/5 for n = 0 mod 5, n >= 10
+    (Cor. 12) and n = 5 (Remark 13), gamma >= ceil(22n/5) for n >= 10 (Theorem 11); the path
+    DP gives n <= 7; sampled rows of the resident powers are checked against the oracle."""
+    torch = torch_mod
+    m = 10
+    A, n = rd.transfer_matrix(m)
+    assert n == 64769
+    ld = A.stride(0)
+    kmax = 48
+    work = rd.power_workspace(n, ld, kmax, 8)
+    plan = rd.sparse_plan(A, n, n, 2)
+    r = rd.power_until_periodic_sparse(A, n, plan, kmax, work)
+    assert r["found"]
+    g = r["gamma"]
+
+    def gamma(nn):
+        if nn <= r["j"]:
+            return int(g[nn])
+        k, p, q = r["k"], r["p"], r["q"]
+        return int(g[k + (nn - k) % p]) + q * ((nn - k) // p)
+
+    for nn in range(3, 8):
+        assert gamma(nn) == orc.row_dp(m, nn), nn
+    assert gamma(5) == 22
+    for nn in range(10, 401):
+        assert 5 * gamma(nn) >= 22 * nn, nn
+        if nn % 5 == 0:
+            assert 5 * gamma(nn) == 22 * nn, nn
+    rng = np.random.default_rng(10)
+    rows = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, 2)]))
+    ora = orc.power_rows(m, rows, r["j"])
+    for k in range(r["j"] - 2, r["j"] + 1):
+        off = rd.power_slot(n, ld, kmax, work.numel(), k)
+        pk = work[off:off + n * ld * 2].view(torch.int16).view(n, ld)[rows.tolist(), :n].cpu().numpy()
+        want = ora[k - 1]
+        fin = want != INF64
+        assert np.array_equal(pk == I16_INF, ~fin)
+        d = want[fin] - pk[fin].astype(np.int64)
+        assert np.all(d == d[0]), k
+    del work, plan, A
+    torch.cuda.empty_cache()
+    assert rd.gamma_R(m, 100) == 440 and rd.gamma_R(m, 7) == orc.row_dp(m, 7)
