@@ -88,6 +88,21 @@ rd_status rd_enumerate_states(int m, uint32_t *codes_dev, uint8_t *weights_dev, 
 rd_status rd_build_transfer(int m, int16_t *A_dev, int64_t lda, cudaStream_t s);
 
 /*
+ * rd_build_transfer_loss -- the matrix of the Appendix (lower bound via the
+ * loss of almost Roman dominating functions on the top m rows, m >= 2; the
+ * paper uses m = 4).  Arcs follow Sec. 4.A except in the last row, where
+ * q_m = d behaves like q_m = c (that row needs no domination); the label is
+ * 10 p(a) + 5 p(b) - 2 nd(q,p) with nd from Algorithm 3 (including the vertex
+ * below the strip when p_m = a), STORED PLUS 2m so that no entry is negative
+ * (each row contributes at least -2).  Then A'^n = (2mn) (x) A^n:
+ * 2 L_a(n) = min diag A'^n - 2mn, and a relation A'^(k+p) = q' (x) A'^k means
+ * A^(k+p) = (q' - 2mp) (x) A^k.  Readings of two typos: the word factors are
+ * those of Definition 4, and the last-row case q_m = b reads "or p_m = d".
+ * Layout and errors as rd_build_transfer.
+ */
+rd_status rd_build_transfer_loss(int m, int16_t *A_dev, int64_t lda, cudaStream_t s);
+
+/*
  * rd_minplus_gemm -- C = A (x) B, the (min,+) product of Sec. 3:
  * C[i][j] = min_t (A[i][t] + B[t][j]), for an M x K matrix A, a K x N matrix B
  * and an M x N result C (C may not alias A or B).  Operands follow the
@@ -151,11 +166,12 @@ rd_status rd_power_slot(int64_t N, int64_t lda, int kmax, size_t work_bytes, int
  *
  * Block-sparse form of an M x K operand A: rows in blocks of R consecutive rows
  * (R in {1, 2, 4, 8}); for block b, entries block_start[b] .. block_start[b+1]-1
- * list, in increasing order, the columns t (entry_col) where some row of the
- * block is finite, and entry_w[e*R + r] holds A[b*R + r][t] in both halfwords
- * (RD_INF when that row has no arc to t).  All three arrays are device memory
- * owned by the caller: block_start has ceil(M/R) + 1 int64, entry_col has
- * `entries` uint32 and entry_w has entries * R uint32.
+ * list, in increasing order, the columns t where some row of the block is
+ * finite.  Entry e is a record of rd_sparse_record_words(R) uint32 words at
+ * records[e * words]: word 0 = t, word 1 + r = A[b*R + r][t] in both halfwords
+ * (RD_INF when that row has no arc to t), the rest zero.  Both arrays are
+ * device memory owned by the caller: block_start has ceil(M/R) + 1 int64 and
+ * records has entries * words uint32 (16-byte aligned).
  *
  * rd_sparse_count -- fills block_start (exclusive prefix sums of the per-block
  * entry counts; block_start[ceil(M/R)] = total) and returns the total in
@@ -164,18 +180,20 @@ rd_status rd_power_slot(int64_t N, int64_t lda, int kmax, size_t work_bytes, int
 rd_status rd_sparse_count(const int16_t *A, int64_t lda, int64_t M, int64_t K, int R, int64_t *block_start_dev,
                           int64_t *entries_host, cudaStream_t s);
 
-/* rd_sparse_build -- fills entry_col and entry_w from A and the block_start of rd_sparse_count. */
+/* rd_sparse_record_words -- 32-bit words per entry record for R (2, 4, 8 or 12); 0 for an invalid R. */
+int rd_sparse_record_words(int R);
+
+/* rd_sparse_build -- fills the records from A and the block_start of rd_sparse_count. */
 rd_status rd_sparse_build(const int16_t *A, int64_t lda, int64_t M, int64_t K, int R, const int64_t *block_start_dev,
-                          uint32_t *entry_col_dev, uint32_t *entry_w_dev, cudaStream_t s);
+                          uint32_t *records_dev, cudaStream_t s);
 
 /*
  * rd_sparse_minplus -- C = A (x) B (Sec. 3) with A (M x K) in block-sparse form
  * and B a dense K x N matrix (ldb), C dense M x N (ldc); same conventions and
  * min_out as rd_minplus_gemm.  C may not alias B.
  */
-rd_status rd_sparse_minplus(int R, int64_t M, const int64_t *block_start, const uint32_t *entry_col,
-                            const uint32_t *entry_w, const int16_t *B, int64_t ldb, int64_t N, int16_t *C, int64_t ldc,
-                            int32_t *min_out, cudaStream_t s);
+rd_status rd_sparse_minplus(int R, int64_t M, const int64_t *block_start, const uint32_t *records, const int16_t *B,
+                            int64_t ldb, int64_t N, int16_t *C, int64_t ldc, int32_t *min_out, cudaStream_t s);
 
 /*
  * rd_power_until_periodic_sparse -- rd_power_until_periodic (same work buffer,
@@ -184,10 +202,9 @@ rd_status rd_sparse_minplus(int R, int64_t M, const int64_t *block_start, const 
  * A_dev is still read once, for the first power.
  */
 rd_status rd_power_until_periodic_sparse(const int16_t *A_dev, int64_t N, int64_t lda, int R,
-                                         const int64_t *block_start, const uint32_t *entry_col,
-                                         const uint32_t *entry_w, int kmax, void *work_dev, size_t work_bytes,
-                                         int64_t *gamma_host, int32_t *k_out, int32_t *p_out, int64_t *q_out,
-                                         cudaStream_t s);
+                                         const int64_t *block_start, const uint32_t *records, int kmax,
+                                         void *work_dev, size_t work_bytes, int64_t *gamma_host, int32_t *k_out,
+                                         int32_t *p_out, int64_t *q_out, cudaStream_t s);
 
 /*
  * rd_sparse_tune -- autotuner for the rows per block R of the sparse step: for

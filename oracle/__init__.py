@@ -73,6 +73,14 @@ def _load():
             lib.rdo_row_dp.restype = i64
             lib.rdo_gamma_direct.argtypes = [ctypes.c_int, ctypes.c_int, vp]
             lib.rdo_gamma_direct.restype = ctypes.c_int
+            lib.rdo_follows_loss.argtypes = [ctypes.c_int, u32, u32]
+            lib.rdo_follows_loss.restype = ctypes.c_int
+            lib.rdo_nd.argtypes = [ctypes.c_int, u32, u32]
+            lib.rdo_nd.restype = ctypes.c_int
+            lib.rdo_transfer_loss.argtypes = [ctypes.c_int, vp, i64]
+            lib.rdo_transfer_loss.restype = ctypes.c_int
+            lib.rdo_brute_force_loss.argtypes = [ctypes.c_int, ctypes.c_int]
+            lib.rdo_brute_force_loss.restype = i64
             lib.rdo_transfer_rows.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp]
             lib.rdo_transfer_rows.restype = ctypes.c_int
             _ = i32
@@ -219,6 +227,31 @@ def row_dp(m: int, n: int) -> int:
     """gamma_R(P_m box C_n) by dynamic programming along the path (independent of the column words)."""
     r = _load().rdo_row_dp(m, n)
     if r < 0:
+        raise ValueError("size out of range")
+    return int(r)
+
+
+def transfer_loss(m: int) -> np.ndarray:
+    """The Appendix variant's matrix: labels 10 p(a) + 5 p(b) - 2 nd(q,p) (raw, may be negative), INF off arcs."""
+    n = num_words(m)
+    a = np.empty((n, n), dtype=np.int64)
+    assert _load().rdo_transfer_loss(m, _ptr(a), n) == 0
+    return a
+
+
+def nd(m: int, q: int, p: int) -> int:
+    """Algorithm 3: vertices newly dominated by column p after column q."""
+    return int(_load().rdo_nd(m, q, p))
+
+
+def follows_loss(m: int, q: int, p: int) -> bool:
+    return bool(_load().rdo_follows_loss(m, q, p))
+
+
+def brute_force_loss(m: int, n: int) -> int:
+    """2 L_a(n) on the m-row strip by exhaustive search over the Appendix's definition (mn <= 20)."""
+    r = _load().rdo_brute_force_loss(m, n)
+    if r == -(2 ** 63):
         raise ValueError("size out of range")
     return int(r)
 

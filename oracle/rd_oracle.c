@@ -560,3 +560,110 @@ int rdo_transfer_rows(int m, const int64_t *rows, int nrows, int64_t *out) {
   free(wt);
   return 0;
 }
+
+/* ======================================================================
+ * Appendix variant: almost Roman dominating functions on the top m rows of a
+ * tall cylinder (the paper uses m = 4).  Vertices of the last row need not be
+ * dominated, and the arc label counts the loss 5 g - 2 |D(g)|.
+ * ====================================================================== */
+
+/*
+ * "p can follow q" for the variant (Appendix, conditions for a word to follow
+ * another): rows 1..m-1 as in Sec. 4.A; in the last row, q_m = d no longer
+ * forces p_m = a and behaves like q_m = c.  Readings of two typos: the
+ * forbidden factors are ad, da, ab, ba, bb as in Definition 4 (the appendix
+ * prints "ac, ca"), and the last-row case q_m = b reads "or p_m = d" (printed
+ * "p_3 = d").
+ */
+int rdo_follows_loss(int m, uint32_t q, uint32_t p) {
+  for (int i = 1; i <= m; ++i) {
+    int qi = letter(m, q, i), pi = letter(m, p, i);
+    if (i == m && qi == LD) qi = LC; /* the last row needs no domination */
+    int ok;
+    switch (qi) {
+      case LA: ok = (pi == LA || pi == LC); break;
+      case LB: ok = (pi == LD) || (pi == LC && has_vertical_a(m, p, i)); break;
+      case LC: ok = (pi == LA || pi == LB || pi == LD) || (pi == LC && has_vertical_a(m, p, i)); break;
+      default: ok = (pi == LA); break;
+    }
+    if (!ok) return 0;
+  }
+  return 1;
+}
+
+/* Algorithm 3: nd(q,p), the vertices newly dominated by column p after column q. */
+int rdo_nd(int m, uint32_t q, uint32_t p) {
+  int nd = 0;
+  for (int i = 1; i <= m; ++i) {
+    const int qi = letter(m, q, i), pi = letter(m, p, i);
+    if (qi == LA && pi == LA) nd += 1;
+    else if (qi == LB && pi == LC) nd += 1;
+    else if (qi == LC && pi == LA) nd += 2;
+    else if ((qi == LC || qi == LD) && (pi == LB || pi == LC)) nd += 1;
+    else if (qi == LD && pi == LA) nd += 3;
+  }
+  if (letter(m, p, m) == LA) nd += 1; /* the vertex below the strip */
+  return nd;
+}
+
+/* The variant's matrix: A[q][p] = 10 p(a) + 5 p(b) - 2 nd(q,p) on arcs, else infinity (raw, may be negative). */
+int rdo_transfer_loss(int m, int64_t *A, int64_t N) {
+  int64_t n = rdo_num_words(m);
+  if (n < 0 || n != N) return 1;
+  uint32_t *code = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N);
+  int32_t *wt = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+  if (!code || !wt) { free(code); free(wt); return 2; }
+  rdo_words(m, code, wt, N);
+  for (int64_t q = 0; q < N; ++q)
+    for (int64_t p = 0; p < N; ++p) {
+      if (!rdo_follows_loss(m, code[q], code[p])) { A[q * N + p] = RDO_INF; continue; }
+      int na = 0, nb = 0;
+      for (int i = 1; i <= m; ++i) {
+        na += letter(m, code[p], i) == LA;
+        nb += letter(m, code[p], i) == LB;
+      }
+      A[q * N + p] = 10 * na + 5 * nb - 2 * rdo_nd(m, code[q], code[p]);
+    }
+  free(code);
+  free(wt);
+  return 0;
+}
+
+/*
+ * Exhaustive 2 L_a(n) from the definition (Appendix): the least 5 g(P_m box C_n)
+ * - 2 |D(g)| over g: V -> {0,1,2} such that every 0-vertex outside the last row
+ * has a neighbour valued 2; D(g) = R_1 with N[R_2], neighbourhoods taken in the
+ * taller cylinder, so a 2 in the last row also dominates the vertex below it.
+ * All 3^(mn) assignments are visited (mn <= 20).
+ */
+int64_t rdo_brute_force_loss(int m, int n) {
+  if (m < 2 || n < 3 || m * n > 20) return INT64_MIN;
+  const int V = m * n;
+  int f[20];
+  for (int v = 0; v < V; ++v) f[v] = 0;
+  int64_t best = INT64_MAX;
+  for (;;) {
+    int ok = 1;
+    int64_t w = 0, dom = 0;
+    for (int c = 0; c < n && ok; ++c)
+      for (int r = 0; r < m; ++r) {
+        const int v = c * m + r;
+        w += f[v];
+        int has2 = (f[v] == 2);
+        if (r > 0 && f[v - 1] == 2) has2 = 1;
+        if (r < m - 1 && f[v + 1] == 2) has2 = 1;
+        if (f[((c + 1) % n) * m + r] == 2) has2 = 1;
+        if (f[((c + n - 1) % n) * m + r] == 2) has2 = 1;
+        const int dominated = (f[v] >= 1) || has2;
+        if (!dominated && r < m - 1) { ok = 0; break; }
+        dom += dominated;
+        if (r == m - 1 && f[v] == 2) dom += 1; /* the vertex below, outside the strip */
+      }
+    if (ok && 5 * w - 2 * dom < best) best = 5 * w - 2 * dom;
+    int v = 0;
+    while (v < V && f[v] == 2) f[v++] = 0;
+    if (v == V) break;
+    ++f[v];
+  }
+  return best;
+}

@@ -53,6 +53,7 @@ def _lib():
         lib.rd_padded_dim.argtypes = [i64, vp]
         lib.rd_enumerate_states.argtypes = [ctypes.c_int, vp, vp, vp]
         lib.rd_build_transfer.argtypes = [ctypes.c_int, vp, i64, vp]
+        lib.rd_build_transfer_loss.argtypes = [ctypes.c_int, vp, i64, vp]
         lib.rd_minplus_gemm.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, vp, vp]
         lib.rd_power_work_bytes.argtypes = [i64, i64, ctypes.c_int, ctypes.c_int, vp]
         lib.rd_power_until_periodic.argtypes = [vp, i64, i64, ctypes.c_int, vp, sz, vp, vp, vp, vp, vp]
@@ -60,15 +61,18 @@ def _lib():
         lib.rd_power_slot.argtypes = [i64, i64, ctypes.c_int, sz, ctypes.c_int, vp]
         lib.rd_power_until_periodic_noalloc.argtypes = [vp, i64, i64, ctypes.c_int, vp, vp, vp, vp, vp]
         lib.rd_sparse_count.argtypes = [vp, i64, i64, i64, ctypes.c_int, vp, vp, vp]
-        lib.rd_sparse_build.argtypes = [vp, i64, i64, i64, ctypes.c_int, vp, vp, vp, vp]
-        lib.rd_sparse_minplus.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, i64, i64, vp, i64, vp, vp]
+        lib.rd_sparse_record_words.argtypes = [ctypes.c_int]
+        lib.rd_sparse_record_words.restype = ctypes.c_int
+        lib.rd_sparse_build.argtypes = [vp, i64, i64, i64, ctypes.c_int, vp, vp, vp]
+        lib.rd_sparse_minplus.argtypes = [ctypes.c_int, i64, vp, vp, vp, i64, i64, vp, i64, vp, vp]
+        lib.rd_power_until_periodic_sparse.argtypes = [vp, i64, i64, ctypes.c_int, vp, vp, ctypes.c_int, vp, sz, vp,
+                                                       vp, vp, vp, vp]
         lib.rd_sparse_tune.argtypes = [vp, i64, i64, vp, sz, vp, vp, vp]
-        lib.rd_power_until_periodic_sparse.argtypes = [vp, i64, i64, ctypes.c_int, vp, vp, vp, ctypes.c_int, vp, sz,
-                                                       vp, vp, vp, vp, vp]
         for name in ("rd_state_count", "rd_padded_dim", "rd_enumerate_states", "rd_build_transfer",
                      "rd_minplus_gemm", "rd_power_work_bytes", "rd_power_until_periodic", "rd_gamma_R",
                      "rd_power_slot", "rd_power_until_periodic_noalloc", "rd_sparse_count", "rd_sparse_build",
-                     "rd_sparse_minplus", "rd_power_until_periodic_sparse", "rd_sparse_tune"):
+                     "rd_sparse_minplus", "rd_power_until_periodic_sparse", "rd_sparse_tune",
+                     "rd_build_transfer_loss"):
             getattr(lib, name).restype = st
         _ = i32
         _LIB = lib
@@ -128,6 +132,17 @@ def build_transfer(m: int, A, stream=None) -> None:
     _check(_lib().rd_build_transfer(m, _dptr(A), A.stride(0), _stream(stream)), "rd_build_transfer")
 
 
+def build_transfer_loss(m: int, A, stream=None) -> None:
+    """Fill A with the Appendix variant's matrix, labels shifted by loss_shift(m)."""
+    assert A.dim() == 2 and A.stride(1) == 1
+    _check(_lib().rd_build_transfer_loss(m, _dptr(A), A.stride(0), _stream(stream)), "rd_build_transfer_loss")
+
+
+def loss_shift(m: int) -> int:
+    """The constant rd_build_transfer_loss adds to every label: 2m."""
+    return 2 * m
+
+
 def minplus_gemm(A, B, C, M: int | None = None, N: int | None = None, K: int | None = None, min_out=None,
                  stream=None) -> None:
     """C[:M, :N] = A[:M, :K] (x) B[:K, :N] on int16 CUDA tensors (row-major, unit column stride)."""
@@ -182,10 +197,10 @@ def sparse_count(A, M: int, K: int, R: int, block_start, stream=None) -> int:
     return ent.value
 
 
-def sparse_build(A, M: int, K: int, R: int, block_start, entry_col, entry_w, stream=None) -> None:
-    """Block-sparse form, step 2: entry_col (int32 view of uint32) and entry_w (duplicated weights)."""
-    _check(_lib().rd_sparse_build(_dptr(A), A.stride(0), M, K, R, _dptr(block_start), _dptr(entry_col),
-                                  _dptr(entry_w), _stream(stream)), "rd_sparse_build")
+def sparse_build(A, M: int, K: int, R: int, block_start, records, stream=None) -> None:
+    """Block-sparse form, step 2: the entry records (int32 view of uint32)."""
+    _check(_lib().rd_sparse_build(_dptr(A), A.stride(0), M, K, R, _dptr(block_start), _dptr(records),
+                                  _stream(stream)), "rd_sparse_build")
 
 
 def sparse_plan(A, M: int, K: int, R: int = 4, stream=None) -> dict:
@@ -195,19 +210,19 @@ def sparse_plan(A, M: int, K: int, R: int = 4, stream=None) -> dict:
     nb = (M + R - 1) // R
     start = torch.empty(nb + 1, dtype=torch.int64, device=A.device)
     ent = sparse_count(A, M, K, R, start, stream)
-    col = torch.empty(max(ent, 1), dtype=torch.int32, device=A.device)
-    w = torch.empty(max(ent, 1) * R, dtype=torch.int32, device=A.device)
-    sparse_build(A, M, K, R, start, col, w, stream)
-    return dict(R=R, M=M, K=K, entries=ent, block_start=start, entry_col=col, entry_w=w)
+    words = _lib().rd_sparse_record_words(R)
+    rec = torch.empty(max(ent, 1) * words, dtype=torch.int32, device=A.device)
+    sparse_build(A, M, K, R, start, rec, stream)
+    return dict(R=R, M=M, K=K, entries=ent, block_start=start, records=rec)
 
 
 def sparse_minplus(plan: dict, B, C, N: int | None = None, min_out=None, stream=None) -> None:
     """C[:M, :N] = A (x) B[:K, :N] with A given by sparse_plan()."""
     N = C.shape[1] if N is None else N
     mo = _dptr(min_out) if min_out is not None else None
-    _check(_lib().rd_sparse_minplus(plan["R"], plan["M"], _dptr(plan["block_start"]), _dptr(plan["entry_col"]),
-                                    _dptr(plan["entry_w"]), _dptr(B), B.stride(0), N, _dptr(C), C.stride(0), mo,
-                                    _stream(stream)), "rd_sparse_minplus")
+    _check(_lib().rd_sparse_minplus(plan["R"], plan["M"], _dptr(plan["block_start"]), _dptr(plan["records"]),
+                                    _dptr(B), B.stride(0), N, _dptr(C), C.stride(0), mo, _stream(stream)),
+           "rd_sparse_minplus")
 
 
 def sparse_tune(A, n: int, scratch, stream=None):
@@ -224,7 +239,7 @@ def power_until_periodic_sparse(A, n: int, plan: dict, kmax: int, work, stream=N
     gamma = np.zeros(kmax + 1, dtype=np.int64)
     k, p, q = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
     st = _lib().rd_power_until_periodic_sparse(_dptr(A), n, A.stride(0), plan["R"], _dptr(plan["block_start"]),
-                                               _dptr(plan["entry_col"]), _dptr(plan["entry_w"]), kmax, _dptr(work),
+                                               _dptr(plan["records"]), kmax, _dptr(work),
                                                work.numel() * work.element_size(), ctypes.c_void_p(gamma.ctypes.data),
                                                ctypes.byref(k), ctypes.byref(p), ctypes.byref(q), _stream(stream))
     _check(st, "rd_power_until_periodic_sparse", ok=(RD_OK, RD_NOT_FOUND))

@@ -436,8 +436,7 @@ rd_status compute_cached(int m, Cached* out) {
   }
   const int64_t nb = (N + kR - 1) / kR;
   int64_t* start = nullptr;
-  uint32_t* ecol = nullptr;
-  uint32_t* ew = nullptr;
+  uint32_t* rec = nullptr;
   int64_t entries = 0;
   if (rc == RD_OK) {
     e = cudaMalloc(&start, (size_t)(nb + 1) * sizeof(int64_t));
@@ -448,21 +447,18 @@ rd_status compute_cached(int m, Cached* out) {
   }
   if (rc == RD_OK) rc = rd_sparse_count(A, ld, N, N, kR, start, &entries, s);
   if (rc == RD_OK) {
-    e = cudaMalloc(&ecol, (size_t)(entries > 0 ? entries : 1) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&ew, (size_t)(entries > 0 ? entries : 1) * 4 * kR);
+    e = cudaMalloc(&rec, (size_t)(entries > 0 ? entries : 1) * 4 * rd_sparse_record_words(kR));
     if (e != cudaSuccess) {
       set_cuda_error(e);
       rc = (e == cudaErrorMemoryAllocation) ? RD_ERR_NOMEM : RD_ERR_CUDA;
     }
   }
-  if (rc == RD_OK) rc = rd_sparse_build(A, ld, N, N, kR, start, ecol, ew, s);
+  if (rc == RD_OK) rc = rd_sparse_build(A, ld, N, N, kR, start, rec, s);
   if (rc == RD_OK)
-    rc = rd_power_until_periodic_sparse(A, N, ld, kR, start, ecol, ew, kGammaKmax, work, wbytes, g.data(), &k, &p,
-                                        &q, s);
+    rc = rd_power_until_periodic_sparse(A, N, ld, kR, start, rec, kGammaKmax, work, wbytes, g.data(), &k, &p, &q, s);
   if (s) cudaStreamSynchronize(s);
   if (start) cudaFree(start);
-  if (ecol) cudaFree(ecol);
-  if (ew) cudaFree(ew);
+  if (rec) cudaFree(rec);
   if (A) cudaFree(A);
   if (work) cudaFree(work);
   if (s) cudaStreamDestroy(s);

@@ -8,13 +8,19 @@
 //
 // Block-sparse form of A: the rows are grouped in blocks of R consecutive rows.
 // For each block, the entries are the columns t where any of its R rows has a
-// finite A[i][t] (sorted), each with an R-vector of weights, A[i][t] duplicated
-// into both halfwords of a 32-bit word and RD_INF where row i has no arc to t.
-// The product kernel loads row t of B once per entry and applies it to all R
-// rows, so B is read nnz/(reuse) times instead of nnz times; RD_INF weights
-// cannot lower a minimum (INF + b >= INF >= acc), so the kernel needs no branch
-// per row.  Consecutive words share many successors (R = 4 reads B 1.8x less
-// often, R = 8 2.6x), at the price of R - popcount wasted DPX operations per entry.
+// finite A[i][t] (sorted); each entry is one record of W(R) 32-bit words:
+// {t, w_0, .., w_{R-1}, padding}, w_r = A[b R + r][t] duplicated into both
+// halfwords, RD_INF where row b R + r has no arc to t.  The product kernel loads
+// row t of B once per entry and applies it to all R rows, so B is read
+// nnz/(reuse) times instead of nnz times; RD_INF weights cannot lower a minimum
+// (INF + b >= INF >= acc), so the kernel needs no branch per row.  Consecutive
+// words share many successors (R = 4 reads B 1.8x less often, R = 8 2.6x), at
+// the price of R - popcount wasted DPX operations per entry.
+//
+// The product is bound by the SM's load path (L1/LSU), so the kernel keeps it
+// for B: a CTA stages chunks of records in shared memory with coalesced loads,
+// and each thread owns 16 columns (two 16-byte loads per B row), which halves
+// the per-entry bookkeeping per byte of B.
 #include "rd_internal.cuh"
 
 namespace rd {
@@ -99,11 +105,14 @@ __global__ void exclusive_scan_kernel(int64_t* v, int64_t n) {
   if (threadIdx.x == 0) v[n] = carry;
 }
 
-// One warp per block: the sorted columns and their R-vectors of duplicated weights.
+// 32-bit words per entry record: {t, w_0..w_{R-1}} padded to 8 or 16-byte multiples.
+__host__ __device__ constexpr int record_words(int R) { return R == 1 ? 2 : ((1 + R + 3) / 4) * 4; }
+
+// One warp per block: the sorted columns and their R-vectors of duplicated weights, as records.
 template <int R>
 __global__ void sparse_build_kernel(const int16_t* __restrict__ A, int64_t lda, int64_t M, int64_t K, int64_t nb,
-                                    const int64_t* __restrict__ start, uint32_t* __restrict__ ecol,
-                                    uint32_t* __restrict__ ew) {
+                                    const int64_t* __restrict__ start, uint32_t* __restrict__ rec) {
+  constexpr int W = record_words(R);
   const int64_t b = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (b >= nb) return;
@@ -134,9 +143,12 @@ __global__ void sparse_build_kernel(const int16_t* __restrict__ A, int64_t lda, 
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       if ((any >> e) & 1u) {
-        ecol[p] = (uint32_t)(col + e);
+        uint32_t* out = rec + p * W;
+        out[0] = (uint32_t)(col + e);
 #pragma unroll
-        for (int r = 0; r < R; ++r) ew[p * R + r] = half_of(v[r], e) * 0x00010001u;
+        for (int r = 0; r < R; ++r) out[1 + r] = half_of(v[r], e) * 0x00010001u;
+#pragma unroll
+        for (int q = 1 + R; q < W; ++q) out[q] = 0u;
         ++p;
       }
     }
@@ -147,9 +159,8 @@ __global__ void sparse_build_kernel(const int16_t* __restrict__ A, int64_t lda, 
 struct SparseArgs {
   int64_t M;  // rows of the sparse operand and of C
   const int64_t* start;
-  const uint32_t* ecol;
-  const uint32_t* ew;
-  const int16_t* B;  // dense right operand, rows indexed by ecol
+  const uint32_t* rec;  // entry records, record_words(R) words each
+  const int16_t* B;     // dense right operand, rows indexed by the records' t
   int64_t ldb;
   int16_t* C;
   int64_t ldc;
@@ -162,9 +173,16 @@ struct SparseArgs {
   int slots;
 };
 
-// CTA = one block of R rows x (8 * blockDim.x) columns; each thread owns 8 columns (one uint4).
+constexpr int kChunk = 128;  // entry records staged in shared memory at a time
+
+// CTA = one block of R rows x (16 * blockDim.x) columns.  Thread t owns columns
+// [base + 8t, base + 8t + 8) and [base + 8(T + t), base + 8(T + t) + 8), so each of
+// its two loads per B row is part of one contiguous warp-wide sweep.
 template <int R, bool RING>
 __global__ void __launch_bounds__(128) sparse_minplus_kernel(SparseArgs a) {
+  constexpr int W = record_words(R);
+  constexpr int U = (R >= 8) ? 2 : 4;  // entries whose B rows are in flight together
+  __shared__ __align__(16) uint32_t srec[kChunk * W];
   const int16_t* __restrict__ B = a.B;
   int16_t* __restrict__ C = a.C;
   if (RING) {
@@ -173,46 +191,58 @@ __global__ void __launch_bounds__(128) sparse_minplus_kernel(SparseArgs a) {
     B = a.ring + (int64_t)(k % a.slots) * a.slot_elems;
     C = a.ring + (int64_t)((k + 1) % a.slots) * a.slot_elems;
   }
+  const int T = blockDim.x;
   const int64_t b = blockIdx.x;
-  const int64_t col = ((int64_t)blockIdx.y * blockDim.x + threadIdx.x) * 8;
-  const bool colok = col < a.Ncols;
+  const int64_t base = (int64_t)blockIdx.y * T * 16;
+  const int64_t col[2] = {base + threadIdx.x * 8, base + (T + threadIdx.x) * 8};
+  const bool ok0 = col[0] < a.Ncols, ok1 = col[1] < a.Ncols;
   const uint4 inf4 = make_uint4(kInf2, kInf2, kInf2, kInf2);
-  uint32_t acc[R][4];
+  uint32_t acc[R][8];
 #pragma unroll
   for (int r = 0; r < R; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = kInf2;
+    for (int c = 0; c < 8; ++c) acc[r][c] = kInf2;
 
-  const int64_t e1 = a.start[b + 1];
-  int64_t e = a.start[b];
-  // groups of four entries: the four row loads are in flight together
-  for (; e + 4 <= e1; e += 4) {
-    uint4 pv[4];
+  const int64_t e_begin = a.start[b], e_end = a.start[b + 1];
+  for (int64_t c0 = e_begin; c0 < e_end; c0 += kChunk) {
+    const int n_in = (e_end - c0 < kChunk) ? (int)(e_end - c0) : kChunk;
+    __syncthreads();  // the previous chunk has been consumed
+    for (int i = threadIdx.x; i < n_in * W; i += T) srec[i] = __ldg(a.rec + c0 * W + i);
+    __syncthreads();
+    int e = 0;
+    for (; e + U <= n_in; e += U) {
+      uint4 pv[U][2];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const uint32_t t = __ldg(a.ecol + e + u);
-      pv[u] = colok ? __ldg(reinterpret_cast<const uint4*>(B + (int64_t)t * a.ldb + col)) : inf4;
-    }
+      for (int u = 0; u < U; ++u) {
+        const uint32_t t = srec[(e + u) * W];
+        const int16_t* row = B + (int64_t)t * a.ldb;
+        pv[u][0] = ok0 ? __ldg(reinterpret_cast<const uint4*>(row + col[0])) : inf4;
+        pv[u][1] = ok1 ? __ldg(reinterpret_cast<const uint4*>(row + col[1])) : inf4;
+      }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const uint32_t p4[4] = {pv[u].x, pv[u].y, pv[u].z, pv[u].w};
+      for (int u = 0; u < U; ++u) {
+        const uint32_t p8[8] = {pv[u][0].x, pv[u][0].y, pv[u][0].z, pv[u][0].w,
+                                pv[u][1].x, pv[u][1].y, pv[u][1].z, pv[u][1].w};
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const uint32_t w = __ldg(a.ew + (e + u) * R + r);
+        for (int r = 0; r < R; ++r) {
+          const uint32_t w = srec[(e + u) * W + 1 + r];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = __viaddmin_s16x2(p4[c], w, acc[r][c]);
+          for (int c = 0; c < 8; ++c) acc[r][c] = __viaddmin_s16x2(p8[c], w, acc[r][c]);
+        }
       }
     }
-  }
-  for (; e < e1; ++e) {
-    const uint32_t t = __ldg(a.ecol + e);
-    const uint4 pv = colok ? __ldg(reinterpret_cast<const uint4*>(B + (int64_t)t * a.ldb + col)) : inf4;
-    const uint32_t p4[4] = {pv.x, pv.y, pv.z, pv.w};
+    for (; e < n_in; ++e) {
+      const uint32_t t = srec[e * W];
+      const int16_t* row = B + (int64_t)t * a.ldb;
+      const uint4 q0 = ok0 ? __ldg(reinterpret_cast<const uint4*>(row + col[0])) : inf4;
+      const uint4 q1 = ok1 ? __ldg(reinterpret_cast<const uint4*>(row + col[1])) : inf4;
+      const uint32_t p8[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const uint32_t w = __ldg(a.ew + e * R + r);
+      for (int r = 0; r < R; ++r) {
+        const uint32_t w = srec[e * W + 1 + r];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[r][c] = __viaddmin_s16x2(p4[c], w, acc[r][c]);
+        for (int c = 0; c < 8; ++c) acc[r][c] = __viaddmin_s16x2(p8[c], w, acc[r][c]);
+      }
     }
   }
 
@@ -220,21 +250,25 @@ __global__ void __launch_bounds__(128) sparse_minplus_kernel(SparseArgs a) {
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int64_t row = b * R + r;
-    if (row < a.M && colok) {
-      const uint4 out = make_uint4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
-      if (col + 8 <= a.Ncols) {
-        *reinterpret_cast<uint4*>(C + row * a.ldc + col) = out;
+    if (row >= a.M) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!(h == 0 ? ok0 : ok1)) continue;
+      const uint4 out = make_uint4(acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
+      const int64_t c = col[h];
+      if (c + 8 <= a.Ncols) {
+        *reinterpret_cast<uint4*>(C + row * a.ldc + c) = out;
       } else {
 #pragma unroll
         for (int e2 = 0; e2 < 8; ++e2)
-          if (col + e2 < a.Ncols) C[row * a.ldc + col + e2] = (int16_t)half_of(out, e2);
+          if (c + e2 < a.Ncols) C[row * a.ldc + c + e2] = (int16_t)half_of(out, e2);
       }
 #pragma unroll
       for (int e2 = 0; e2 < 8; ++e2) {
-        if (col + e2 < a.Ncols) {
+        if (c + e2 < a.Ncols) {
           const int32_t v = (int32_t)half_of(out, e2);
           lmin = min(lmin, v);
-          if (col + e2 == row) ldiag = min(ldiag, v);
+          if (c + e2 == row) ldiag = min(ldiag, v);
         }
       }
     }
@@ -267,8 +301,9 @@ __global__ void __launch_bounds__(128) sparse_minplus_kernel(SparseArgs a) {
 template <bool RING>
 cudaError_t launch_sparse(int R, const SparseArgs& a, cudaStream_t s) {
   const int64_t nb = (a.M + R - 1) / R;
-  const int threads = (a.Ncols > 32768) ? 64 : 128;  // keeps one slab of B columns within L2
-  const int64_t gy = (a.Ncols + threads * 8 - 1) / (threads * 8);
+  // slab of B columns one wave of CTAs sweeps: 16 * threads columns x Ncols rows must stay well inside L2
+  const int threads = (a.Ncols > 32768) ? 32 : (a.Ncols > 16384 ? 64 : 128);
+  const int64_t gy = (a.Ncols + threads * 16 - 1) / (threads * 16);
   if (nb <= 0 || gy <= 0) return cudaSuccess;
   if (nb > 0x7FFFFFFF || gy > 65535) return cudaErrorInvalidConfiguration;
   const dim3 grid((unsigned)nb, (unsigned)gy);
@@ -285,8 +320,7 @@ cudaError_t launch_sparse(int R, const SparseArgs& a, cudaStream_t s) {
 struct SparsePlan {
   int R;
   const int64_t* start;
-  const uint32_t* ecol;
-  const uint32_t* ew;
+  const uint32_t* rec;
 };
 
 cudaError_t sparse_power_product(const Run& r, const void* ctx, cudaStream_t s) {
@@ -294,8 +328,7 @@ cudaError_t sparse_power_product(const Run& r, const void* ctx, cudaStream_t s) 
   SparseArgs a{};
   a.M = r.N;
   a.start = pl->start;
-  a.ecol = pl->ecol;
-  a.ew = pl->ew;
+  a.rec = pl->rec;
   a.ldb = r.ld;
   a.ldc = r.ld;
   a.Ncols = r.N;
@@ -342,34 +375,37 @@ extern "C" rd_status rd_sparse_count(const int16_t* A, int64_t lda, int64_t M, i
   return RD_OK;
 }
 
+extern "C" int rd_sparse_record_words(int R) { return valid_r(R) ? record_words(R) : 0; }
+
 extern "C" rd_status rd_sparse_build(const int16_t* A, int64_t lda, int64_t M, int64_t K, int R,
-                                     const int64_t* block_start_dev, uint32_t* entry_col_dev, uint32_t* entry_w_dev,
-                                     cudaStream_t s) {
-  if (!A || !block_start_dev || !entry_col_dev || !entry_w_dev || M < 1 || K < 1 || !valid_r(R)) return RD_ERR_ARG;
-  if (lda < K || lda % 8 != 0 || !aligned16(A) || K > 0xFFFFFFFFll) return RD_ERR_ARG;
+                                     const int64_t* block_start_dev, uint32_t* records_dev, cudaStream_t s) {
+  if (!A || !block_start_dev || !records_dev || M < 1 || K < 1 || !valid_r(R)) return RD_ERR_ARG;
+  if (lda < K || lda % 8 != 0 || !aligned16(A) || !aligned16(records_dev) || K > 0xFFFFFFFFll) return RD_ERR_ARG;
   const int64_t nb = (M + R - 1) / R;
   const int warps_per_cta = 8;
   const int64_t ctas = (nb + warps_per_cta - 1) / warps_per_cta;
   if (ctas > 0x7FFFFFFF) return RD_ERR_ARG;
   const unsigned g = (unsigned)ctas, t = 32 * warps_per_cta;
   switch (R) {
-    case 1: sparse_build_kernel<1><<<g, t, 0, s>>>(A, lda, M, K, nb, block_start_dev, entry_col_dev, entry_w_dev); break;
-    case 2: sparse_build_kernel<2><<<g, t, 0, s>>>(A, lda, M, K, nb, block_start_dev, entry_col_dev, entry_w_dev); break;
-    case 4: sparse_build_kernel<4><<<g, t, 0, s>>>(A, lda, M, K, nb, block_start_dev, entry_col_dev, entry_w_dev); break;
-    default: sparse_build_kernel<8><<<g, t, 0, s>>>(A, lda, M, K, nb, block_start_dev, entry_col_dev, entry_w_dev); break;
+    case 1: sparse_build_kernel<1><<<g, t, 0, s>>>(A, lda, M, K, nb, block_start_dev, records_dev); break;
+    case 2: sparse_build_kernel<2><<<g, t, 0, s>>>(A, lda, M, K, nb, block_start_dev, records_dev); break;
+    case 4: sparse_build_kernel<4><<<g, t, 0, s>>>(A, lda, M, K, nb, block_start_dev, records_dev); break;
+    default: sparse_build_kernel<8><<<g, t, 0, s>>>(A, lda, M, K, nb, block_start_dev, records_dev); break;
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e);
   return RD_OK;
 }
 
-extern "C" rd_status rd_sparse_minplus(int R, int64_t M, const int64_t* block_start, const uint32_t* entry_col,
-                                       const uint32_t* entry_w, const int16_t* B, int64_t ldb, int64_t N, int16_t* C,
-                                       int64_t ldc, int32_t* min_out, cudaStream_t s) {
+extern "C" rd_status rd_sparse_minplus(int R, int64_t M, const int64_t* block_start, const uint32_t* records,
+                                       const int16_t* B, int64_t ldb, int64_t N, int16_t* C, int64_t ldc,
+                                       int32_t* min_out, cudaStream_t s) {
   if (!valid_r(R) || M < 0 || N < 0) return RD_ERR_ARG;
   if (M > 0 && N > 0) {
-    if (!block_start || !entry_col || !entry_w || !B || !C) return RD_ERR_ARG;
-    if (!aligned16(B) || !aligned16(C) || ldb < N || ldb % 8 != 0 || ldc < N || ldc % 8 != 0) return RD_ERR_ARG;
+    if (!block_start || !records || !B || !C) return RD_ERR_ARG;
+    if (!aligned16(B) || !aligned16(C) || !aligned16(records) || ldb < N || ldb % 8 != 0 || ldc < N ||
+        ldc % 8 != 0)
+      return RD_ERR_ARG;
   }
   cudaError_t e = cudaSuccess;
   if (min_out) {
@@ -380,8 +416,7 @@ extern "C" rd_status rd_sparse_minplus(int R, int64_t M, const int64_t* block_st
   SparseArgs a{};
   a.M = M;
   a.start = block_start;
-  a.ecol = entry_col;
-  a.ew = entry_w;
+  a.rec = records;
   a.B = B;
   a.ldb = ldb;
   a.C = C;
@@ -394,15 +429,14 @@ extern "C" rd_status rd_sparse_minplus(int R, int64_t M, const int64_t* block_st
 }
 
 extern "C" rd_status rd_power_until_periodic_sparse(const int16_t* A_dev, int64_t N, int64_t lda, int R,
-                                                    const int64_t* block_start, const uint32_t* entry_col,
-                                                    const uint32_t* entry_w, int kmax, void* work_dev,
-                                                    size_t work_bytes, int64_t* gamma_host, int32_t* k_out,
-                                                    int32_t* p_out, int64_t* q_out, cudaStream_t s) {
-  if (!A_dev || !block_start || !entry_col || !entry_w || !work_dev || !gamma_host || !k_out || !p_out || !q_out)
-    return RD_ERR_ARG;
+                                                    const int64_t* block_start, const uint32_t* records, int kmax,
+                                                    void* work_dev, size_t work_bytes, int64_t* gamma_host,
+                                                    int32_t* k_out, int32_t* p_out, int64_t* q_out, cudaStream_t s) {
+  if (!A_dev || !block_start || !records || !work_dev || !gamma_host || !k_out || !p_out || !q_out) return RD_ERR_ARG;
   if (N < 1 || lda < N || lda % 8 != 0 || kmax < 1 || kmax > (1 << 20) || !valid_r(R)) return RD_ERR_ARG;
-  if (!aligned16(A_dev) || (reinterpret_cast<uintptr_t>(work_dev) & 255u) != 0) return RD_ERR_ARG;
-  const SparsePlan plan{R, block_start, entry_col, entry_w};
+  if (!aligned16(A_dev) || !aligned16(records) || (reinterpret_cast<uintptr_t>(work_dev) & 255u) != 0)
+    return RD_ERR_ARG;
+  const SparsePlan plan{R, block_start, records};
   return power_search(A_dev, N, lda, kmax, work_dev, work_bytes, sparse_power_product, &plan, gamma_host, k_out,
                       p_out, q_out, s);
 }
@@ -437,20 +471,20 @@ extern "C" rd_status rd_sparse_tune(const int16_t* A, int64_t lda, int64_t N, vo
     int64_t entries = 0;
     rc = rd_sparse_count(A, lda, N, N, R, start, &entries, s);
     if (rc != RD_OK) break;
-    const size_t col_bytes = round_up((size_t)entries * 4, 256), w_bytes = round_up((size_t)entries * 4 * R, 256);
-    if (start_bytes + col_bytes + w_bytes > plan_room) continue;  // this candidate does not fit: skipped
-    uint32_t* ecol = reinterpret_cast<uint32_t*>(plan_base + start_bytes);
-    uint32_t* ew = reinterpret_cast<uint32_t*>(plan_base + start_bytes + col_bytes);
-    rc = rd_sparse_build(A, lda, N, N, R, start, ecol, ew, s);
+    const size_t rec_bytes = round_up((size_t)entries * 4 * record_words(R), 256);
+    if (start_bytes + rec_bytes > plan_room) continue;  // this candidate does not fit: skipped
+    uint32_t* rec = reinterpret_cast<uint32_t*>(plan_base + start_bytes);
+    rc = rd_sparse_build(A, lda, N, N, R, start, rec, s);
     if (rc != RD_OK) break;
     // A (x) A moves the same bytes and does the same DPX work as A (x) P_k.
-    rc = rd_sparse_minplus(R, N, start, ecol, ew, A, lda, N, C, lda, nullptr, s);  // warm-up
+    rc = rd_sparse_minplus(R, N, start, rec, A, lda, N, C, lda, nullptr, s);  // warm-up
     if (rc != RD_OK) break;
     e = cudaEventRecord(e0, s);
     for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
-      rc = rd_sparse_minplus(R, N, start, ecol, ew, A, lda, N, C, lda, nullptr, s);
+      rc = rd_sparse_minplus(R, N, start, rec, A, lda, N, C, lda, nullptr, s);
       if (rc != RD_OK) break;
     }
+    if (rc != RD_OK) break;
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.f;

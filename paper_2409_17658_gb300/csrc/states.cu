@@ -106,10 +106,26 @@ __global__ void enumerate_kernel(WordTable w, int64_t n, uint32_t* codes, uint8_
   weights[r] = (uint8_t)word_weight(word_masks(code, w.m));
 }
 
+// Appendix variant: the last row (bit 0) needs no domination, so q_m = d follows the q_m = c rule.
+__device__ inline Masks relax_last_row(Masks q) {
+  q.c |= q.d & 1u;
+  q.d &= ~1u;
+  return q;
+}
+
+// Algorithm 3, all rows at once: newly dominated vertices of column p after column q,
+// plus the vertex below the strip when p_m = a.
+__device__ inline int newly_dominated(const Masks& q, const Masks& p) {
+  return __popc(q.a & p.a) + __popc(q.b & p.c) + 2 * __popc(q.c & p.a) + __popc((q.c | q.d) & (p.b | p.c)) +
+         3 * __popc(q.d & p.a) + (int)(p.a & 1u);
+}
+
 // Tile of 64 rows (q) x 256 columns (p).  Thread (tx, ty): columns 8 tx .. 8 tx + 7,
-// rows ty, ty + 8, ..., one 16-byte store per row.
+// rows ty, ty + 8, ..., one 16-byte store per row.  LOSS selects the Appendix variant,
+// whose labels 10 p(a) + 5 p(b) - 2 nd(q,p) are stored shifted by 2m (never negative).
 constexpr int kTq = 64, kTp = 256;
 
+template <bool LOSS>
 __global__ void __launch_bounds__(256) transfer_kernel(WordTable w, int64_t n, int16_t* A, int64_t lda,
                                                        int64_t ptiles) {
   __shared__ Masks qm[kTq];
@@ -142,13 +158,20 @@ __global__ void __launch_bounds__(256) transfer_kernel(WordTable w, int64_t n, i
   for (int r = ty; r < kTq; r += 8) {
     const int64_t q = q0 + r;
     if (q >= n) break;
+    const Masks qf = LOSS ? relax_last_row(qm[r]) : qm[r];
     uint32_t packed[4];
 #pragma unroll
     for (int e = 0; e < 8; e += 2) {
-      const int j0 = 8 * tx + e, j1 = j0 + 1;
-      const int16_t v0 = (p0 + j0 < n && can_follow(qm[r], pm[j0], full)) ? pw[j0] : kInf;
-      const int16_t v1 = (p0 + j1 < n && can_follow(qm[r], pm[j1], full)) ? pw[j1] : kInf;
-      packed[e / 2] = (uint32_t)(uint16_t)v0 | ((uint32_t)(uint16_t)v1 << 16);
+      int16_t v[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = 8 * tx + e + h;
+        const bool arc = (p0 + j < n) && can_follow(qf, pm[j], full);
+        int label = pw[j];
+        if (LOSS) label = 10 * __popc(pm[j].a) + 5 * __popc(pm[j].b) - 2 * newly_dominated(qm[r], pm[j]) + 2 * w.m;
+        v[h] = arc ? (int16_t)label : kInf;
+      }
+      packed[e / 2] = (uint32_t)(uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
     }
     *reinterpret_cast<uint4*>(A + q * lda + pc) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
   }
@@ -200,7 +223,21 @@ extern "C" rd_status rd_build_transfer(int m, int16_t* A_dev, int64_t lda, cudaS
   const int64_t ptiles = (lda + kTp - 1) / kTp, qtiles = (n + kTq - 1) / kTq;
   const int64_t tiles = ptiles * qtiles;
   if (tiles > 0x7FFFFFFF) return RD_ERR_ARG;
-  transfer_kernel<<<(unsigned)tiles, 256, 0, s>>>(w, n, A_dev, lda, ptiles);
+  transfer_kernel<false><<<(unsigned)tiles, 256, 0, s>>>(w, n, A_dev, lda, ptiles);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
+  return RD_OK;
+}
+
+extern "C" rd_status rd_build_transfer_loss(int m, int16_t* A_dev, int64_t lda, cudaStream_t s) {
+  int64_t n = 0;
+  if (m < 2 || rd_state_count(m, &n) != RD_OK || !A_dev) return RD_ERR_ARG;
+  if (lda < n || lda % 8 != 0 || !aligned16(A_dev)) return RD_ERR_ARG;
+  const WordTable w = make_table(m);
+  const int64_t ptiles = (lda + kTp - 1) / kTp, qtiles = (n + kTq - 1) / kTq;
+  const int64_t tiles = ptiles * qtiles;
+  if (tiles > 0x7FFFFFFF) return RD_ERR_ARG;
+  transfer_kernel<true><<<(unsigned)tiles, 256, 0, s>>>(w, n, A_dev, lda, ptiles);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
   return RD_OK;

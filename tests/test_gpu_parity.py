@@ -397,3 +397,40 @@ def test_power_m10(rd, torch_mod, orc):
     del work, plan, A
     torch.cuda.empty_cache()
     assert rd.gamma_R(m, 100) == 440 and rd.gamma_R(m, 7) == orc.row_dp(m, 7)
+
+
+# ---------------------------------------------------------------- f2: Appendix loss variant
+
+@pytest.mark.parametrize("m", [2, 3, 4, 5, 6])
+def test_transfer_loss_matrix(rd, torch_mod, orc, m):
+    torch = torch_mod
+    n = rd.state_count(m)
+    A = torch.empty((n, rd.padded_dim(n)), dtype=torch.int16, device="cuda")
+    rd.build_transfer_loss(m, A)
+    want = orc.transfer_loss(m)
+    shifted = np.where(want == INF64, INF64, want + rd.loss_shift(m))
+    got = A.cpu().numpy()
+    assert np.array_equal(got[:, :n], to_i16(shifted))
+    assert np.all(got[:, n:] == I16_INF)
+
+
+@pytest.mark.parametrize("m", [4, 5, 6])
+@pytest.mark.parametrize("sparse", [False, True])
+def test_loss_variant_power(rd, torch_mod, orc, m, sparse):
+    torch = torch_mod
+    n = rd.state_count(m)
+    A = torch.empty((n, rd.padded_dim(n)), dtype=torch.int16, device="cuda")
+    rd.build_transfer_loss(m, A)
+    work = rd.power_workspace(n, A.stride(0), 48, 8)
+    if sparse:
+        r = rd.power_until_periodic_sparse(A, n, rd.sparse_plan(A, n, n, 2), 48, work)
+    else:
+        r = rd.power_until_periodic(A, n, 48, work)
+    s = rd.loss_shift(m)
+    o = orc.power_until_periodic(0, a=orc.transfer_loss(m), kmax=48)
+    assert r["found"] and o["found"]
+    assert (r["k"], r["p"], r["q"] - s * r["p"]) == (o["k"], o["p"], o["q"])
+    j = r["j"]
+    assert np.array_equal(r["gamma"][1:j + 1] - s * np.arange(1, j + 1), o["gamma"][1:j + 1])
+    if m == 4:
+        assert (r["k"], r["p"], r["q"] - s * r["p"]) == (30, 1, 1)  # the Appendix's relation
