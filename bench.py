@@ -220,6 +220,125 @@ def run_sparse_only(rd, torch, args) -> None:
                       "b_row_TBps": plan["entries"] * n * 2 / (ms * 1e-3) / 1e12}))
 
 
+def batched_products(rd, torch, count: int = 64, seed: int = 4) -> dict:
+    """Config of 64 independent products, N_i = round(exp(U[ln 128, ln 8192])) (seeded): one persistent
+    batched launch against one launch per product, both on the same stream, results compared."""
+    from paper_2409_17658_gb300 import inputs
+
+    sizes = inputs.log_uniform_sizes(count, 128, 8192, seed=seed)
+    ops = float(sum(n ** 3 for n in sizes))
+    probs, refs = [], []
+    for i, n in enumerate(sizes):
+        ld = (n + 7) // 8 * 8
+        A = inputs.matrix_torch(n, n, seed=1000 + 2 * i, ld=ld, device="cuda")
+        B = inputs.matrix_torch(n, n, seed=1001 + 2 * i, ld=ld, device="cuda")
+        probs.append((A, B, torch.empty_like(A), n, n, n))
+        refs.append(torch.empty_like(A))
+    stream = torch.cuda.current_stream()
+
+    def one_by_one():
+        for (A, B, _, n, _, _), R in zip(probs, refs):
+            rd.minplus_gemm(A, B, R, n, n, n)
+
+    def batched():
+        rd.minplus_gemm_batched(probs)
+
+    out = {"products": count, "sizes_min_median_max": [min(sizes), int(np.median(sizes)), max(sizes)],
+           "addmins": ops}
+    for name, fn in (("one_launch_per_product", one_by_one), ("batched_persistent", batched)):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms": ms, "gops": ops / (ms * 1e-3) / 1e9, "launches": count if name.startswith("one") else 2}
+    out["speedup"] = out["one_launch_per_product"]["ms"] / out["batched_persistent"]["ms"]
+    out["results_identical"] = bool(all(torch.equal(p[2][:, :p[4]], r[:, :p[4]]) for p, r in zip(probs, refs)))
+    del probs, refs
+    torch.cuda.empty_cache()
+
+    # A(G) for m = 1..9 powered until periodic: all together (CUDA graph of 8 steps) vs one after another
+    kmax, R = 64, 2
+    runs = []
+    for m in range(1, 10):
+        A, n = rd.transfer_matrix(m)
+        runs.append((A, n, rd.sparse_plan(A, n, n, R), rd.power_workspace(n, A.stride(0), kmax, 8)))
+    timings = {}
+    for name in ("sequential", "together_graph"):
+        for _ in range(2):  # first pass untimed
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if name == "sequential":
+                res = [rd.power_until_periodic_sparse(A, n, plan, kmax, w) for A, n, plan, w in runs]
+            else:
+                res = rd.power_until_periodic_multi(runs, R, kmax, graph_steps=8)
+            torch.cuda.synchronize()
+            timings[name] = time.perf_counter() - t0
+        timings[name + "_triples"] = [(r["k"], r["p"], r["q"]) for r in res]
+    out["periods_m1_to_9"] = {"sequential_s": timings["sequential"], "together_graph_s": timings["together_graph"],
+                              "speedup": timings["sequential"] / timings["together_graph"],
+                              "same_results": timings["sequential_triples"] == timings["together_graph_triples"],
+                              "triples": timings["together_graph_triples"]}
+    del runs
+    torch.cuda.empty_cache()
+    return out
+
+
+def serving(rd, queries: int = 20000, rate: float = 20000.0, seed: int = 7, budget_gb: float = 120.0) -> dict:
+    """A Poisson stream of gamma_R(P_m box C_n) queries through the query server.
+
+    m uniform in {2..9} and n uniform in [3, 200]; one query in 20 is m = 10 with n = 0 mod 5 (its
+    footprint, 76 GB, fits the budget).  Phase "cold" starts from a fresh server (first queries of each m
+    trigger its period search; searches share the GPU step by step); phase "warm" replays the stream
+    against the settled server.  Latency is measured by the server from submit to answer.
+    """
+    from paper_2409_17658_gb300 import inputs
+
+    x = inputs.splitmix64((np.uint64(seed) << np.uint64(32)) + np.arange(4 * queries, dtype=np.uint64))
+    u = (x >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    gaps = -np.log1p(-u[:queries]) / rate
+    arrivals = np.cumsum(gaps)
+    ms = (2 + (u[queries:2 * queries] * 8).astype(np.int64)).astype(np.int32)
+    ns = (3 + (u[2 * queries:3 * queries] * 198).astype(np.int64)).astype(np.int64)
+    ten = u[3 * queries:] < 0.05
+    ms[ten] = 10
+    ns[ten] = 10 + 5 * (ns[ten] % 39)
+    out = {"queries": queries, "rate_per_s": rate, "budget_gb": budget_gb}
+    sv = rd.Server(hbm_budget_bytes=int(budget_gb * (1 << 30)), kmax=128)
+    try:
+        for phase in ("cold", "warm"):
+            tickets = []
+            t0 = time.perf_counter()
+            i = 0
+            while i < queries:
+                now = time.perf_counter() - t0
+                j = int(np.searchsorted(arrivals, now, side="right"))
+                if j <= i:
+                    time.sleep(max(0.0, min(arrivals[i] - now, 0.001)))
+                    continue
+                tickets.append(sv.submit(ms[i:j], ns[i:j]))
+                i = j
+            g, st, lat = sv.wait(np.concatenate(tickets), timeout_s=900)
+            wall = time.perf_counter() - t0
+            out[phase] = {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                          "max_ms": float(lat.max() * 1e3), "queries_per_s": queries / wall, "wall_s": wall,
+                          "all_ok": bool(np.all(st == rd.RD_OK))}
+        out["stats"] = sv.stats()
+    finally:
+        sv.close()
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(np.nonzero(ms <= 9)[0], 200, replace=False)
+    out["answers_match_alone"] = bool(all(g[i] == rd.gamma_R(int(ms[i]), int(ns[i])) for i in pick))
+    tens = np.nonzero(ms == 10)[0]
+    out["m10_cor12_holds"] = bool(all(5 * g[i] == 22 * ns[i] for i in tens))
+    return out
+
+
 def run_reference(args, rank, world) -> None:
     """--impl reference: the oracle on the same workload, one bounded row sample per step."""
     if rank != 0:
@@ -258,6 +377,8 @@ def main() -> None:
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-period", action="store_true", help="skip the time-to-period leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timings")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-products leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the query-server leg")
     ap.add_argument("--gemm-only", type=int, default=0, metavar="N",
                     help="time only the product at size N (used for profiler captures)")
     ap.add_argument("--sparse-only", type=int, default=0, metavar="M",
@@ -380,6 +501,10 @@ def main() -> None:
     del bufs
 
     extra = {}
+    if rank == 0 and not args.no_serving:
+        extra["serving"] = serving(rd)
+    if rank == 0 and not args.no_batched:
+        extra["batched"] = batched_products(rd, torch)
     if rank == 0 and not args.no_period:
         extra["time_to_period"] = time_to_period(rd, torch, [3, 7, 9, 10], with_oracle=not args.no_cpu)
     if rank == 0 and not args.no_cpu:

@@ -116,6 +116,27 @@ rd_status rd_minplus_gemm(const int16_t *A, int64_t lda, const int16_t *B, int64
                           int64_t M, int64_t N, int64_t K, int32_t *min_out, cudaStream_t s);
 
 /*
+ * rd_minplus_gemm_batched -- `count` (<= 128) independent products
+ * C_i = A_i (x) B_i, each with the conventions of rd_minplus_gemm (min_out may
+ * be null), in one persistent launch: two CTAs per SM walk the concatenated
+ * tile list of all products, longest tiles (largest K) first, so small products
+ * run side by side and the tail of a large one is filled by others.  The
+ * problem table travels in the kernel's parameters (no device copy).
+ */
+typedef struct {
+  const int16_t *A;
+  int64_t lda;
+  const int16_t *B;
+  int64_t ldb;
+  int16_t *C;
+  int64_t ldc;
+  int64_t M, N, K;
+  int32_t *min_out;
+} rd_gemm_problem;
+
+rd_status rd_minplus_gemm_batched(const rd_gemm_problem *problems, int count, cudaStream_t s);
+
+/*
  * rd_power_work_bytes -- size of the work buffer rd_power_until_periodic needs
  * to keep `slots` normalised powers (slots >= 2) of an N x N matrix with
  * leading dimension ld, for at most kmax powers.  A relation with period p
@@ -218,6 +239,77 @@ rd_status rd_power_until_periodic_sparse(const int16_t *A_dev, int64_t N, int64_
  */
 rd_status rd_sparse_tune(const int16_t *A, int64_t lda, int64_t N, void *scratch_dev, size_t scratch_bytes,
                          int *best_R, float *ms_per_R, cudaStream_t s);
+
+/*
+ * rd_power_until_periodic_multi -- up to 16 period searches advanced together
+ * (for instance A(G) for m = 1..9).  Each run has its own operand A (dense, for
+ * the first power), its block-sparse form (the same R for all runs), its own
+ * work buffer (rd_power_work_bytes) and its own outputs, with the meaning of
+ * rd_power_until_periodic_sparse; `status` receives that call's status for the
+ * run.  One step of all runs is four launches (a product over every run's
+ * CTAs, then normaliser/hash, finalize and compare side by side); stopped runs
+ * exit at kernel entry.  graph_steps > 0 captures that many steps into one CUDA
+ * graph (on a private stream ordered after s) and replays it until every run
+ * has stopped; 0 launches the steps directly.  Returns RD_OK when the batch ran
+ * (per-run results in runs[i].status), RD_ERR_ARG / RD_ERR_NOMEM / RD_ERR_CUDA
+ * otherwise.  Synchronous.
+ */
+typedef struct {
+  const int16_t *A;
+  int64_t N;
+  int64_t lda;
+  const int64_t *block_start;
+  const uint32_t *records;
+  void *work;
+  size_t work_bytes;
+  int64_t *gamma_host; /* kmax + 1 entries */
+  int32_t k, p;        /* outputs */
+  int64_t q;
+  rd_status status;
+} rd_power_run;
+
+rd_status rd_power_until_periodic_multi(rd_power_run *runs, int count, int R, int kmax, int graph_steps,
+                                        cudaStream_t s);
+
+/*
+ * Query server with continuous batching (for many gamma_R(P_m box C_n) queries).
+ * A worker thread on the device current at creation keeps one period-search job
+ * per m that has been asked for and is not settled yet.  Each step advances all
+ * admitted jobs together (rd_power_until_periodic_multi's launches); queries are
+ * answered as soon as gamma(n) is known -- power n computed, or the relation
+ * (k, p, q) found, after which the m is answered on the host by Prop. 7 for the
+ * life of the server and its device memory is freed.  Jobs are admitted in
+ * arrival order while their device footprint (A(G), block-sparse form with
+ * R = 2, work buffer with 8 powers) fits hbm_budget_bytes; a job larger than the
+ * whole budget answers RD_ERR_NOMEM.  At most 16 jobs run at once.  The server
+ * allocates and frees its own device memory.
+ */
+typedef struct rd_server rd_server;
+typedef struct {
+  uint64_t submitted, answered, steps, jobs_admitted, jobs_completed;
+  size_t bytes_in_use, bytes_peak;
+} rd_server_stats_t;
+
+/* rd_server_create -- start a server; kmax (8..4096) bounds the powers per m. */
+rd_status rd_server_create(size_t hbm_budget_bytes, int kmax, rd_server **out);
+
+/* rd_server_submit -- enqueue `count` queries (m[i] in [1, RD_MAX_M], n[i] >= 3); tickets out.  Thread-safe. */
+rd_status rd_server_submit(rd_server *sv, int count, const int32_t *m, const int64_t *n, uint64_t *tickets);
+
+/*
+ * rd_server_wait -- wait (up to timeout_s seconds in total) for the given
+ * tickets; on RD_OK fills gamma[i], status[i] (the query's own rd_status) and
+ * latency_s[i] (submit to answer, nullable) and forgets the tickets.
+ * RD_ERR_TIMEOUT when some ticket was not answered in time (none is forgotten).
+ * Thread-safe.
+ */
+rd_status rd_server_wait(rd_server *sv, int count, const uint64_t *tickets, double timeout_s, int64_t *gamma,
+                         int32_t *status, double *latency_s);
+
+rd_status rd_server_stats(rd_server *sv, rd_server_stats_t *out);
+
+/* rd_server_destroy -- stop the worker, free its device memory; unanswered tickets are dropped. */
+rd_status rd_server_destroy(rd_server *sv);
 
 /*
  * rd_power_until_periodic_noalloc -- the same search as rd_power_until_periodic

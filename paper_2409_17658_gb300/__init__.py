@@ -54,6 +54,13 @@ def _lib():
         lib.rd_enumerate_states.argtypes = [ctypes.c_int, vp, vp, vp]
         lib.rd_build_transfer.argtypes = [ctypes.c_int, vp, i64, vp]
         lib.rd_build_transfer_loss.argtypes = [ctypes.c_int, vp, i64, vp]
+        lib.rd_minplus_gemm_batched.argtypes = [vp, ctypes.c_int, vp]
+        lib.rd_power_until_periodic_multi.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
+        lib.rd_server_create.argtypes = [sz, ctypes.c_int, vp]
+        lib.rd_server_submit.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+        lib.rd_server_wait.argtypes = [vp, ctypes.c_int, vp, ctypes.c_double, vp, vp, vp]
+        lib.rd_server_stats.argtypes = [vp, vp]
+        lib.rd_server_destroy.argtypes = [vp]
         lib.rd_minplus_gemm.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, vp, vp]
         lib.rd_power_work_bytes.argtypes = [i64, i64, ctypes.c_int, ctypes.c_int, vp]
         lib.rd_power_until_periodic.argtypes = [vp, i64, i64, ctypes.c_int, vp, sz, vp, vp, vp, vp, vp]
@@ -72,7 +79,9 @@ def _lib():
                      "rd_minplus_gemm", "rd_power_work_bytes", "rd_power_until_periodic", "rd_gamma_R",
                      "rd_power_slot", "rd_power_until_periodic_noalloc", "rd_sparse_count", "rd_sparse_build",
                      "rd_sparse_minplus", "rd_power_until_periodic_sparse", "rd_sparse_tune",
-                     "rd_build_transfer_loss"):
+                     "rd_build_transfer_loss", "rd_minplus_gemm_batched", "rd_power_until_periodic_multi",
+                     "rd_server_create", "rd_server_submit", "rd_server_wait", "rd_server_stats",
+                     "rd_server_destroy"):
             getattr(lib, name).restype = st
         _ = i32
         _LIB = lib
@@ -154,6 +163,106 @@ def minplus_gemm(A, B, C, M: int | None = None, N: int | None = None, K: int | N
     mo = _dptr(min_out) if min_out is not None else None
     _check(_lib().rd_minplus_gemm(_dptr(A), A.stride(0), _dptr(B), B.stride(0), _dptr(C), C.stride(0), M, N, K,
                                   mo, _stream(stream)), "rd_minplus_gemm")
+
+
+class GemmProblem(ctypes.Structure):
+    """rd_gemm_problem of include/rd.h."""
+    _fields_ = [("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64),
+                ("C", ctypes.c_void_p), ("ldc", ctypes.c_int64), ("M", ctypes.c_int64), ("N", ctypes.c_int64),
+                ("K", ctypes.c_int64), ("min_out", ctypes.c_void_p)]
+
+
+def minplus_gemm_batched(problems, stream=None) -> None:
+    """problems: list of (A, B, C) or (A, B, C, M, N, K, min_out) -- all products in one persistent launch."""
+    arr = (GemmProblem * max(1, len(problems)))()
+    for i, pr in enumerate(problems):
+        A, B, C = pr[:3]
+        M = pr[3] if len(pr) > 3 else C.shape[0]
+        N = pr[4] if len(pr) > 4 else C.shape[1]
+        K = pr[5] if len(pr) > 5 else A.shape[1]
+        mo = pr[6] if len(pr) > 6 else None
+        arr[i] = GemmProblem(A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0), C.data_ptr(), C.stride(0), M, N,
+                             K, mo.data_ptr() if mo is not None else None)
+    _check(_lib().rd_minplus_gemm_batched(arr, len(problems), _stream(stream)), "rd_minplus_gemm_batched")
+
+
+class PowerRun(ctypes.Structure):
+    """rd_power_run of include/rd.h."""
+    _fields_ = [("A", ctypes.c_void_p), ("N", ctypes.c_int64), ("lda", ctypes.c_int64),
+                ("block_start", ctypes.c_void_p), ("records", ctypes.c_void_p), ("work", ctypes.c_void_p),
+                ("work_bytes", ctypes.c_size_t), ("gamma_host", ctypes.c_void_p), ("k", ctypes.c_int32),
+                ("p", ctypes.c_int32), ("q", ctypes.c_int64), ("status", ctypes.c_int)]
+
+
+def power_until_periodic_multi(runs, R: int, kmax: int, graph_steps: int = 8, stream=None) -> list:
+    """runs: list of (A, n, plan, work).  All searches advance together; returns one result dict per run."""
+    arr = (PowerRun * len(runs))()
+    gammas = []
+    for i, (A, n, plan, work) in enumerate(runs):
+        assert plan["R"] == R
+        g = np.zeros(kmax + 1, dtype=np.int64)
+        gammas.append(g)
+        arr[i] = PowerRun(A.data_ptr(), n, A.stride(0), plan["block_start"].data_ptr(), plan["records"].data_ptr(),
+                          work.data_ptr(), work.numel() * work.element_size(), g.ctypes.data, 0, 0, 0, 0)
+    _check(_lib().rd_power_until_periodic_multi(arr, len(runs), R, kmax, graph_steps, _stream(stream)),
+           "rd_power_until_periodic_multi")
+    out = []
+    for i in range(len(runs)):
+        st = arr[i].status
+        _check(st, f"rd_power_until_periodic_multi run {i}", ok=(RD_OK, RD_NOT_FOUND))
+        found = st == RD_OK
+        out.append(dict(status=st, found=found, k=arr[i].k if found else None, p=arr[i].p if found else None,
+                        q=arr[i].q if found else None, j=arr[i].k + arr[i].p if found else kmax, gamma=gammas[i]))
+    return out
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("answered", ctypes.c_uint64), ("steps", ctypes.c_uint64),
+                ("jobs_admitted", ctypes.c_uint64), ("jobs_completed", ctypes.c_uint64),
+                ("bytes_in_use", ctypes.c_size_t), ("bytes_peak", ctypes.c_size_t)]
+
+
+class Server:
+    """rd_server_*: gamma_R queries answered with continuous batching of the period searches."""
+
+    def __init__(self, hbm_budget_bytes: int, kmax: int = 256):
+        h = ctypes.c_void_p()
+        _check(_lib().rd_server_create(hbm_budget_bytes, kmax, ctypes.byref(h)), "rd_server_create")
+        self._h = h
+
+    def submit(self, ms, ns) -> np.ndarray:
+        ms = np.ascontiguousarray(ms, dtype=np.int32)
+        ns = np.ascontiguousarray(ns, dtype=np.int64)
+        t = np.zeros(len(ms), dtype=np.uint64)
+        _check(_lib().rd_server_submit(self._h, len(ms), ms.ctypes.data, ns.ctypes.data, t.ctypes.data),
+               "rd_server_submit")
+        return t
+
+    def wait(self, tickets, timeout_s: float = 600.0):
+        """(gamma, status, latency_s) arrays for the tickets; raises RdError(RD_ERR_TIMEOUT) on timeout."""
+        tickets = np.ascontiguousarray(tickets, dtype=np.uint64)
+        g = np.zeros(len(tickets), dtype=np.int64)
+        st = np.zeros(len(tickets), dtype=np.int32)
+        lat = np.zeros(len(tickets), dtype=np.float64)
+        _check(_lib().rd_server_wait(self._h, len(tickets), tickets.ctypes.data, timeout_s, g.ctypes.data,
+                                     st.ctypes.data, lat.ctypes.data), "rd_server_wait")
+        return g, st, lat
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(_lib().rd_server_stats(self._h, ctypes.byref(s)), "rd_server_stats")
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def close(self) -> None:
+        if self._h:
+            _lib().rd_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def power_work_bytes(n: int, ld: int, kmax: int, slots: int) -> int:

@@ -51,39 +51,16 @@ __device__ __forceinline__ uint32_t pack2(int16_t lo, int16_t hi) {
   return (uint32_t)(uint16_t)lo | ((uint32_t)(uint16_t)hi << 16);
 }
 
-template <bool RING>
-__global__ void __launch_bounds__(NT, 2) minplus_gemm_kernel(GemmParams p) {
-  extern __shared__ __align__(16) uint32_t smem[];
+// One BM x BN output tile of C = A (x) B at (m0, n0), plus its contribution to the
+// minimum (min_out) and the diagonal minimum (diag_out) when those are not null.
+__device__ __forceinline__ void gemm_tile(const int16_t* __restrict__ Ag, const int16_t* __restrict__ Bg,
+                                          int16_t* __restrict__ Cg, const int64_t M, const int64_t N,
+                                          const int64_t K, const int64_t lda, const int64_t ldb, const int64_t ldc,
+                                          const int64_t m0, const int64_t n0, int32_t* min_out, int32_t* diag_out,
+                                          uint32_t* smem) {
   uint32_t* As = smem;                 // [2][BK][BM]
   uint32_t* Bs = smem + 2 * AS_WORDS;  // [BSTAGES][BK][BN/2]
-
-  const int16_t* __restrict__ Ag = p.A;
-  int16_t* __restrict__ Cg = p.C;
-  if (RING) {
-    const PowerState* st = p.st;
-    if (*(volatile const int32_t*)&st->done) return;
-    const int k = *(volatile const int32_t*)&st->k;
-    Ag = p.ring + (int64_t)(k % p.slots) * p.slot_elems;
-    Cg = p.ring + (int64_t)((k + 1) % p.slots) * p.slot_elems;
-  }
-  const int16_t* __restrict__ Bg = p.B;
-  const int64_t M = p.M, N = p.N, K = p.K, lda = p.lda, ldb = p.ldb, ldc = p.ldc;
-
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  // Grouped rasterisation: consecutive CTAs cover kGroupM row tiles x a run of column tiles, so a
-  // wave of resident CTAs shares its A panels and B panels in L2 instead of sweeping all of B.
-  int64_t tile_m, tile_n;
-  {
-    const int64_t gx = gridDim.x, gy = gridDim.y;
-    const int64_t linear = (int64_t)blockIdx.y * gx + blockIdx.x;
-    const int64_t per_group = (int64_t)kGroupM * gx;
-    const int64_t first_m = (linear / per_group) * kGroupM;
-    const int64_t group_rows = (gy - first_m < kGroupM) ? (gy - first_m) : kGroupM;
-    const int64_t in_group = linear % per_group;
-    tile_m = first_m + in_group % group_rows;
-    tile_n = in_group / group_rows;
-  }
-  const int64_t m0 = tile_m * BM, n0 = tile_n * BN;
   const int KT = (int)((K + BK - 1) / BK);
 
   // ---- staging helpers
@@ -188,7 +165,7 @@ __global__ void __launch_bounds__(NT, 2) minplus_gemm_kernel(GemmParams p) {
   // ---- epilogue: store, and reduce the minimum and the diagonal minimum
   uint32_t vmin = kInf2;
   int32_t dmin = kInf;
-  const bool want_diag = (p.diag_out != nullptr) && (m0 < n0 + BN) && (n0 < m0 + BM);
+  const bool want_diag = (diag_out != nullptr) && (m0 < n0 + BN) && (n0 < m0 + BM);
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     const int64_t gi = m0 + ty * 8 + r;
@@ -214,7 +191,7 @@ __global__ void __launch_bounds__(NT, 2) minplus_gemm_kernel(GemmParams p) {
       }
     }
   }
-  if (p.min_out != nullptr || want_diag) {
+  if (min_out != nullptr || want_diag) {
     int32_t lm = min((int32_t)(vmin & 0xFFFF), (int32_t)(vmin >> 16));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -233,22 +210,106 @@ __global__ void __launch_bounds__(NT, 2) minplus_gemm_kernel(GemmParams p) {
         bm = min(bm, red_m[w]);
         bd = min(bd, red_d[w]);
       }
-      if (p.min_out != nullptr && bm < kInf) atomicMin(p.min_out, bm);
-      if (want_diag && bd < kInf) atomicMin(p.diag_out, bd);
+      if (min_out != nullptr && bm < kInf) atomicMin(min_out, bm);
+      if (want_diag && bd < kInf) atomicMin(diag_out, bd);
     }
   }
 }
 
-__global__ void fill_i32_kernel(int32_t* dst, int32_t v) { *dst = v; }
+// Grouped rasterisation: consecutive tiles cover kGroupM row tiles x a run of column tiles, so a
+// wave of resident CTAs shares its A panels and B panels in L2 instead of sweeping all of B.
+__device__ __forceinline__ void grouped_tile(int64_t linear, int64_t gx, int64_t gy, int64_t* tile_m,
+                                             int64_t* tile_n) {
+  const int64_t per_group = (int64_t)kGroupM * gx;
+  const int64_t first_m = (linear / per_group) * kGroupM;
+  const int64_t group_rows = (gy - first_m < kGroupM) ? (gy - first_m) : kGroupM;
+  const int64_t in_group = linear % per_group;
+  *tile_m = first_m + in_group % group_rows;
+  *tile_n = in_group / group_rows;
+}
 
 template <bool RING>
+__global__ void __launch_bounds__(NT, 2) minplus_gemm_kernel(GemmParams p) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int16_t* Ag = p.A;
+  int16_t* Cg = p.C;
+  if (RING) {
+    const PowerState* st = p.st;
+    if (*(volatile const int32_t*)&st->done) return;
+    const int k = *(volatile const int32_t*)&st->k;
+    Ag = p.ring + (int64_t)(k % p.slots) * p.slot_elems;
+    Cg = p.ring + (int64_t)((k + 1) % p.slots) * p.slot_elems;
+  }
+  int64_t tm, tn;
+  grouped_tile((int64_t)blockIdx.y * gridDim.x + blockIdx.x, gridDim.x, gridDim.y, &tm, &tn);
+  gemm_tile(Ag, p.B, Cg, p.M, p.N, p.K, p.lda, p.ldb, p.ldc, tm * BM, tn * BN, p.min_out, p.diag_out, smem);
+}
+
+// ---- batched products: one persistent launch over the tiles of up to kMaxBatch products
+
+constexpr int kMaxBatch = 128;
+
+struct BatchProblem {
+  const int16_t* A;
+  const int16_t* B;
+  int16_t* C;
+  int64_t lda, ldb, ldc, M, N, K;
+  int32_t* min_out;
+  int64_t tiles_m, tiles_n;
+};
+
+struct BatchParams {
+  int count;
+  int64_t tile_start[kMaxBatch + 1];  // prefix sums of the tile counts, in schedule order
+  BatchProblem p[kMaxBatch];
+};
+
+// CTA c takes tiles c, c + gridDim.x, ... of the concatenated tile list.  Problems are
+// ordered by decreasing K (tile cost), so the round robin hands out the long tiles first.
+__global__ void __launch_bounds__(NT, 2) minplus_gemm_batched_kernel(const __grid_constant__ BatchParams bp) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int64_t total = bp.tile_start[bp.count];
+  for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+    int lo = 0, hi = bp.count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (bp.tile_start[mid] <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchProblem& q = bp.p[lo];
+    int64_t tm, tn;
+    grouped_tile(t - bp.tile_start[lo], q.tiles_n, q.tiles_m, &tm, &tn);
+    __syncthreads();  // the previous tile's shared memory is no longer read
+    gemm_tile(q.A, q.B, q.C, q.M, q.N, q.K, q.lda, q.ldb, q.ldc, tm * BM, tn * BN, q.min_out, nullptr, smem);
+  }
+}
+
+struct MinOutList {
+  int count;
+  int32_t* p[kMaxBatch];
+};
+
+__global__ void fill_min_outs_kernel(const __grid_constant__ MinOutList l) {
+  for (int i = threadIdx.x; i < l.count; i += blockDim.x)
+    if (l.p[i] != nullptr) *l.p[i] = kInf;
+}
+
+__global__ void fill_i32_kernel(int32_t* dst, int32_t v) { *dst = v; }
+
+template <int WHICH>  // 0 plain, 1 ring, 2 batched
 cudaError_t set_smem_attr() {
   static int done_dev[64] = {0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < 64 && done_dev[dev]) return cudaSuccess;
-  e = cudaFuncSetAttribute(minplus_gemm_kernel<RING>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  if (WHICH == 0)
+    e = cudaFuncSetAttribute(minplus_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  else if (WHICH == 1)
+    e = cudaFuncSetAttribute(minplus_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  else
+    e = cudaFuncSetAttribute(minplus_gemm_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done_dev[dev] = 1;
   return e;
 }
@@ -267,11 +328,11 @@ cudaError_t launch_minplus_gemm(const GemmParams& p, bool ring, cudaStream_t s) 
   const dim3 grid((unsigned)gx, (unsigned)gy);
   cudaError_t e;
   if (ring) {
-    e = set_smem_attr<true>();
+    e = set_smem_attr<1>();
     if (e != cudaSuccess) return e;
     minplus_gemm_kernel<true><<<grid, NT, SMEM_BYTES, s>>>(p);
   } else {
-    e = set_smem_attr<false>();
+    e = set_smem_attr<0>();
     if (e != cudaSuccess) return e;
     minplus_gemm_kernel<false><<<grid, NT, SMEM_BYTES, s>>>(p);
   }
@@ -303,6 +364,69 @@ extern "C" rd_status rd_minplus_gemm(const int16_t* A, int64_t lda, const int16_
   p.A = A; p.lda = lda; p.B = B; p.ldb = ldb; p.C = C; p.ldc = ldc;
   p.M = M; p.N = N; p.K = K; p.min_out = min_out; p.diag_out = nullptr;
   e = launch_minplus_gemm(p, false, s);
+  if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
+  return RD_OK;
+}
+
+extern "C" rd_status rd_minplus_gemm_batched(const rd_gemm_problem* problems, int count, cudaStream_t s) {
+  if (count < 0 || count > kMaxBatch || (count > 0 && !problems)) return RD_ERR_ARG;
+  if (count == 0) return RD_OK;
+  MinOutList mins{};
+  mins.count = count;
+  int order[kMaxBatch];
+  for (int i = 0; i < count; ++i) {
+    const rd_gemm_problem& q = problems[i];
+    if (q.M < 0 || q.N < 0 || q.K < 0) return RD_ERR_ARG;
+    if (q.M > 0 && q.N > 0) {
+      if (!q.C || !aligned16(q.C) || q.ldc < q.N || q.ldc % 8 != 0) return RD_ERR_ARG;
+      if (q.K > 0 && (!q.A || !q.B || !aligned16(q.A) || !aligned16(q.B) || q.lda < q.K || q.lda % 8 != 0 ||
+                      q.ldb < q.N || q.ldb % 8 != 0))
+        return RD_ERR_ARG;
+    }
+    mins.p[i] = q.min_out;
+    order[i] = i;
+  }
+  // schedule order: decreasing K (the cost of one tile), stable
+  for (int i = 1; i < count; ++i)
+    for (int j = i; j > 0 && problems[order[j]].K > problems[order[j - 1]].K; --j) {
+      const int t = order[j];
+      order[j] = order[j - 1];
+      order[j - 1] = t;
+    }
+  BatchParams bp{};
+  bp.count = 0;
+  bp.tile_start[0] = 0;
+  for (int i = 0; i < count; ++i) {
+    const rd_gemm_problem& q = problems[order[i]];
+    if (q.M == 0 || q.N == 0) continue;
+    BatchProblem& b = bp.p[bp.count];
+    b.A = q.A;
+    b.B = q.B;
+    b.C = q.C;
+    b.lda = q.lda;
+    b.ldb = q.ldb;
+    b.ldc = q.ldc;
+    b.M = q.M;
+    b.N = q.N;
+    b.K = q.K;
+    b.min_out = q.min_out;
+    b.tiles_m = (q.M + BM - 1) / BM;
+    b.tiles_n = (q.N + BN - 1) / BN;
+    bp.tile_start[bp.count + 1] = bp.tile_start[bp.count] + b.tiles_m * b.tiles_n;
+    ++bp.count;
+  }
+  fill_min_outs_kernel<<<1, 128, 0, s>>>(mins);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
+  if (bp.count == 0) return RD_OK;
+  e = set_smem_attr<2>();
+  if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t total = bp.tile_start[bp.count];
+  const int64_t grid = total < 2 * (int64_t)sms ? total : 2 * (int64_t)sms;  // two resident CTAs per SM
+  minplus_gemm_batched_kernel<<<(unsigned)grid, NT, SMEM_BYTES, s>>>(bp);
+  e = cudaGetLastError();
   if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
   return RD_OK;
 }

@@ -95,6 +95,22 @@ rd_status power_search(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, v
                        ProductFn product, const void* ctx, int64_t* gamma_host, int32_t* k_out, int32_t* p_out,
                        int64_t* q_out, cudaStream_t s);
 
+// One period-search run as the multi-run kernels see it (power_multi.cu).
+struct RunDesc {
+  PowerState* st;
+  int16_t* ring;
+  int64_t slot_elems;
+  int slots;
+  int64_t N, ld;
+  const int16_t* A;
+  const int64_t* start;
+  const uint32_t* rec;
+  int64_t nb_unused, slabs_unused;  // filled in by the launcher
+};
+constexpr int kMaxRunsPerStep = 16;
+cudaError_t runs_first(const RunDesc* runs, int count, int R, int kmax, cudaStream_t s);
+cudaError_t runs_step(const RunDesc* runs, int count, int R, cudaStream_t s);
+
 void set_cuda_error(cudaError_t e);
 bool aligned16(const void* p);
 

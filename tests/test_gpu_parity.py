@@ -434,3 +434,62 @@ def test_loss_variant_power(rd, torch_mod, orc, m, sparse):
     assert np.array_equal(r["gamma"][1:j + 1] - s * np.arange(1, j + 1), o["gamma"][1:j + 1])
     if m == 4:
         assert (r["k"], r["p"], r["q"] - s * r["p"]) == (30, 1, 1)  # the Appendix's relation
+
+
+# ---------------------------------------------------------------- batched products (one persistent launch)
+
+def test_minplus_gemm_batched(rd, torch_mod, orc):
+    torch = torch_mod
+    from paper_2409_17658_gb300 import inputs
+
+    rng = np.random.default_rng(77)
+    shapes = [(int(rng.integers(1, 400)), int(rng.integers(1, 600)), int(rng.integers(1, 500))) for _ in range(24)]
+    shapes += [(0, 16, 16), (16, 16, 0), (300, 257, 129)]
+    probs, want = [], []
+    for i, (M, N, K) in enumerate(shapes):
+        dist = ("wide", "u32", "dense")[i % 3]
+        a = inputs.matrix(M, K, seed=100 + i, dist=dist) if M and K else np.zeros((M, K), np.int16)
+        b = inputs.matrix(K, N, seed=200 + i, dist=dist) if K and N else np.zeros((K, N), np.int16)
+        A = upload(torch, a, junk=-3) if M and K else torch.zeros((max(M, 1), 8), dtype=torch.int16, device="cuda")
+        B = upload(torch, b, junk=-3) if K and N else torch.zeros((max(K, 1), (N + 7) // 8 * 8 or 8),
+                                                                 dtype=torch.int16, device="cuda")
+        C = torch.full((max(M, 1), (N + 7) // 8 * 8), 555, dtype=torch.int16, device="cuda")
+        mn = torch.zeros(1, dtype=torch.int32, device="cuda")
+        probs.append((A, B, C, M, N, K, mn))
+        if M and N:
+            w = orc.minplus_i16(a, b) if K else np.full((M, N), I16_INF, np.int32)
+        else:
+            w = None
+        want.append(w)
+    rd.minplus_gemm_batched(probs)
+    torch.cuda.synchronize()
+    for (A, B, C, M, N, K, mn), w in zip(probs, want):
+        if w is None:
+            assert torch.all(C == 555)
+            continue
+        got = C.cpu().numpy()
+        assert np.array_equal(got[:M, :N].astype(np.int32), w), (M, N, K)
+        assert np.all(got[:M, N:] == 555)
+        assert mn.item() == w.min()
+
+
+# ---------------------------------------------------------------- several searches advanced together
+
+@pytest.mark.parametrize("graph_steps", [0, 8])
+def test_power_multi_equals_single_runs(rd, torch_mod, orc, graph_steps):
+    torch = torch_mod
+    kmax = 48
+    runs, singles = [], []
+    for m in range(1, 10):
+        A, n = rd.transfer_matrix(m)
+        plan = rd.sparse_plan(A, n, n, 2)
+        runs.append((A, n, plan, rd.power_workspace(n, A.stride(0), kmax, 8)))
+    res = rd.power_until_periodic_multi(runs, 2, kmax, graph_steps=graph_steps)
+    for m, (A, n, plan, _), r in zip(range(1, 10), runs, res):
+        alone = rd.power_until_periodic_sparse(A, n, plan, kmax, rd.power_workspace(n, A.stride(0), kmax, 8))
+        assert (r["k"], r["p"], r["q"]) == (alone["k"], alone["p"], alone["q"]), m
+        assert np.array_equal(r["gamma"], alone["gamma"]), m
+        if m <= 7:
+            o = orc.power_until_periodic(m, kmax=kmax)
+            assert (r["k"], r["p"], r["q"]) == (o["k"], o["p"], o["q"]), m
+    assert (res[8]["k"], res[8]["p"], res[8]["q"]) == (22, 5, 20)
