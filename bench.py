@@ -38,9 +38,9 @@ SEED_A, SEED_B = 1, 2
 # (measured 126.6 add-mins/clock/SM in a register-resident loop) x 2 add-mins per lane x 2070 MHz.
 SMS, DPX_LANES_PER_CLK, ADDMIN_PER_LANE, SM_MAX_MHZ = 152, 64, 2, 2070.0
 PEAK_GOPS = SMS * DPX_LANES_PER_CLK * ADDMIN_PER_LANE * SM_MAX_MHZ * 1e6 / 1e9
-# DRAM bytes (read + write) per launch of the product kernel at N = 16384 from the ncu capture
-# summarised in profiles/minplus_gemm_n16384.md; None until that capture matches the current kernel.
-GEMM_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) per launch of the product kernel at N = 16384, from the one-pass ncu
+# capture summarised in profiles/minplus_gemm_n16384_dram.md (8.60 GB read + 0.536 GB written).
+GEMM_TRAFFIC_BYTES = 9.136e9
 CONFIG_NAME = "synthetic dense (min,+) GEMM N=16384, int16 uniform[0,32], P(inf)=0.5"
 
 
