@@ -201,7 +201,7 @@ rd_status rd_power_slot(int64_t N, int64_t lda, int kmax, size_t work_bytes, int
 rd_status rd_sparse_count(const int16_t *A, int64_t lda, int64_t M, int64_t K, int R, int64_t *block_start_dev,
                           int64_t *entries_host, cudaStream_t s);
 
-/* rd_sparse_record_words -- 32-bit words per entry record for R (2, 4, 8 or 12); 0 for an invalid R. */
+/* rd_sparse_record_words -- 32-bit words per entry record for R (4, 4, 8 or 12); 0 for an invalid R. */
 int rd_sparse_record_words(int R);
 
 /* rd_sparse_build -- fills the records from A and the block_start of rd_sparse_count. */
@@ -217,10 +217,24 @@ rd_status rd_sparse_minplus(int R, int64_t M, const int64_t *block_start, const 
                             int64_t ldb, int64_t N, int16_t *C, int64_t ldc, int32_t *min_out, cudaStream_t s);
 
 /*
+ * rd_sparse_minplus_tma -- the same product as rd_sparse_minplus, with the rows
+ * of B streamed into shared memory by bulk copies (cp.async.bulk) through a
+ * 16-stage ring guarded by mbarriers: a producer warp per CTA issues the copies,
+ * two consumer warps apply them.  Every device-side wait is bounded; if one runs
+ * out, the value 8 is OR-ed into *err_dev (a device int32 the caller zeroes) and
+ * C is not valid.  Measured on GB300 it is slower than rd_sparse_minplus (m = 9,
+ * R = 2: 15.4 ms against 5.0 ms; one 2 KB row segment per stage does not amortise
+ * the per-copy work), so the period searches use rd_sparse_minplus's kernel.
+ */
+rd_status rd_sparse_minplus_tma(int R, int64_t M, const int64_t *block_start, const uint32_t *records,
+                                const int16_t *B, int64_t ldb, int64_t N, int16_t *C, int64_t ldc, int32_t *min_out,
+                                int32_t *err_dev, cudaStream_t s);
+
+/*
  * rd_power_until_periodic_sparse -- rd_power_until_periodic (same work buffer,
  * outputs and errors) with the power step R = A (x) P_k on the block-sparse form
- * of the same A (built from A_dev with rd_sparse_count / rd_sparse_build).
- * A_dev is still read once, for the first power.
+ * of the same A (built from A_dev with rd_sparse_count / rd_sparse_build), run by
+ * the kernel of rd_sparse_minplus.  A_dev is still read once, for the first power.
  */
 rd_status rd_power_until_periodic_sparse(const int16_t *A_dev, int64_t N, int64_t lda, int R,
                                          const int64_t *block_start, const uint32_t *records, int kmax,

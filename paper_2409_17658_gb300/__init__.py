@@ -75,13 +75,14 @@ def _lib():
         lib.rd_power_until_periodic_sparse.argtypes = [vp, i64, i64, ctypes.c_int, vp, vp, ctypes.c_int, vp, sz, vp,
                                                        vp, vp, vp, vp]
         lib.rd_sparse_tune.argtypes = [vp, i64, i64, vp, sz, vp, vp, vp]
+        lib.rd_sparse_minplus_tma.argtypes = [ctypes.c_int, i64, vp, vp, vp, i64, i64, vp, i64, vp, vp, vp]
         for name in ("rd_state_count", "rd_padded_dim", "rd_enumerate_states", "rd_build_transfer",
                      "rd_minplus_gemm", "rd_power_work_bytes", "rd_power_until_periodic", "rd_gamma_R",
                      "rd_power_slot", "rd_power_until_periodic_noalloc", "rd_sparse_count", "rd_sparse_build",
                      "rd_sparse_minplus", "rd_power_until_periodic_sparse", "rd_sparse_tune",
                      "rd_build_transfer_loss", "rd_minplus_gemm_batched", "rd_power_until_periodic_multi",
                      "rd_server_create", "rd_server_submit", "rd_server_wait", "rd_server_stats",
-                     "rd_server_destroy"):
+                     "rd_server_destroy", "rd_sparse_minplus_tma"):
             getattr(lib, name).restype = st
         _ = i32
         _LIB = lib
@@ -341,6 +342,15 @@ def sparse_tune(A, n: int, scratch, stream=None):
     _check(_lib().rd_sparse_tune(_dptr(A), A.stride(0), n, _dptr(scratch), scratch.numel() * scratch.element_size(),
                                  ctypes.byref(best), ms, _stream(stream)), "rd_sparse_tune")
     return best.value, {R: ms[i] for i, R in enumerate((1, 2, 4, 8)) if ms[i] >= 0}
+
+
+def sparse_minplus_tma(plan: dict, B, C, err, N: int | None = None, min_out=None, stream=None) -> None:
+    """sparse_minplus through the bulk-copy kernel; err is a zeroed device int32 that receives 8 on a timeout."""
+    N = C.shape[1] if N is None else N
+    mo = _dptr(min_out) if min_out is not None else None
+    _check(_lib().rd_sparse_minplus_tma(plan["R"], plan["M"], _dptr(plan["block_start"]), _dptr(plan["records"]),
+                                        _dptr(B), B.stride(0), N, _dptr(C), C.stride(0), mo, _dptr(err),
+                                        _stream(stream)), "rd_sparse_minplus_tma")
 
 
 def power_until_periodic_sparse(A, n: int, plan: dict, kmax: int, work, stream=None) -> dict:

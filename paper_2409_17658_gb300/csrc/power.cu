@@ -149,7 +149,7 @@ rd_status power_search(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, v
   *k_out = 0;
   *p_out = 0;
   *q_out = 0;
-  if (h.done == 3) return (h.err & 1) ? RD_ERR_RANGE : RD_ERR_NOMEM;
+  if (h.done == 3) return status_from_err(h.err);
   return RD_NOT_FOUND;
 }
 

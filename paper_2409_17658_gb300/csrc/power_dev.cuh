@@ -180,7 +180,7 @@ __device__ __forceinline__ void finalize_body(PowerState* st) {
     gam[kn] = (st->dmin >= kInf) ? RD_GAMMA_INF : off[kn - 1] + st->dmin;
     hs[kn] = hk;
     if (st->range_bad) {
-      st->err |= 1;
+      st->err |= kErrRange;
       st->done = 3;
     }
   }
@@ -189,12 +189,12 @@ __device__ __forceinline__ void finalize_body(PowerState* st) {
   for (int i = 1 + (int)threadIdx.x; i < kn; i += 32) {
     if (hs[i] != hk) continue;
     if (kn - i >= st->slots) {
-      atomicOr(&st->err, 2);  // the matching power has left the ring: cannot verify
+      atomicOr(&st->err, kErrRing);  // the matching power has left the ring: cannot verify
       continue;
     }
     const int slot = atomicAdd(&st->ncand, 1);
     if (slot < kMaxCand) st->cand[slot] = i;
-    else atomicOr(&st->err, 4);
+    else atomicOr(&st->err, kErrCandidates);
   }
   __syncwarp();
   if (threadIdx.x == 0 && st->err) st->done = 3;

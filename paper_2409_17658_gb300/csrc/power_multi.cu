@@ -328,7 +328,7 @@ extern "C" rd_status rd_power_until_periodic_multi(rd_power_run* runs, int count
       u.q = h[i].found_q;
       u.status = RD_OK;
     } else if (h[i].done == 3) {
-      u.status = (h[i].err & 1) ? RD_ERR_RANGE : RD_ERR_NOMEM;
+      u.status = status_from_err(h[i].err);
     } else {
       u.status = RD_NOT_FOUND;
     }

@@ -19,7 +19,7 @@ constexpr int kMaxCand = 8;
 struct PowerState {
   int32_t k;            // index of the latest finished normalised power P_k
   int32_t done;         // 0 running, 1 relation found, 2 kmax reached, 3 error
-  int32_t err;          // bit 0 range, bit 1 ring too short, bit 2 too many hash candidates
+  int32_t err;          // kErr* bits: range, ring too short, too many hash candidates, device wait timed out
   int32_t kmax;
   int32_t mu;           // atomicMin target: min of the raw product being formed
   int32_t dmin;         // atomicMin target: min of its diagonal
@@ -38,6 +38,14 @@ constexpr size_t kStateHeader = 256;
 static_assert(sizeof(PowerState) <= kStateHeader, "state header too large");
 
 inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// PowerState::err bits and the status a stopped search reports for them.
+constexpr int32_t kErrRange = 1, kErrRing = 2, kErrCandidates = 4, kErrTimeout = 8;
+inline rd_status status_from_err(int32_t err) {
+  if (err & kErrRange) return RD_ERR_RANGE;
+  if (err & kErrTimeout) return RD_ERR_TIMEOUT;
+  return RD_ERR_NOMEM;
+}
 
 // Layout of the work buffer: [header][offset int64 x (kmax+1)][gamma int64 x (kmax+1)]
 // [hash u64 x (kmax+1)] padded to 256 B, then the ring of power slots.

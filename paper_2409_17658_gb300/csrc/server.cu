@@ -193,7 +193,7 @@ void retire(rd_server* sv, Job* j, const rd::PowerState& h) {
   Final f;
   f.valid = true;
   f.found = (h.done == 1);
-  f.status = (h.done == 1 || h.done == 2) ? RD_OK : ((h.err & 1) ? RD_ERR_RANGE : RD_ERR_NOMEM);
+  f.status = (h.done == 1 || h.done == 2) ? RD_OK : rd::status_from_err(h.err);
   f.k = h.found_i;
   f.p = h.found_j - h.found_i;
   f.q = h.found_q;

@@ -151,6 +151,39 @@ __global__ void __launch_bounds__(128) sparse_minplus_kernel(SparseArgs a) {
   sparse_tile_body<R>(a, B, C, blockIdx.x, blockIdx.y);
 }
 
+template <int R, bool RING>
+__global__ void __launch_bounds__(kTmaThreads) sparse_tma_kernel(SparseArgs a, int32_t* err_plain) {
+  const int16_t* B = a.B;
+  int16_t* C = a.C;
+  int32_t* err = err_plain;
+  if (RING) {
+    if (*(volatile const int32_t*)&a.st->done) return;
+    const int k = *(volatile const int32_t*)&a.st->k;
+    B = a.ring + (int64_t)(k % a.slots) * a.slot_elems;
+    C = a.ring + (int64_t)((k + 1) % a.slots) * a.slot_elems;
+    err = &a.st->err;
+  }
+  if (*(volatile const int32_t*)err & kErrTimeout) return;  // an earlier CTA gave up: the launch is void
+  sparse_tma_tile_body<R>(a, B, C, blockIdx.x, blockIdx.y, err);
+}
+
+template <bool RING>
+cudaError_t launch_sparse_tma(int R, const SparseArgs& a, int32_t* err, cudaStream_t s) {
+  const int64_t nb = (a.M + R - 1) / R;
+  const int64_t gy = (a.Ncols + kSlabCols - 1) / kSlabCols;
+  if (nb <= 0 || gy <= 0) return cudaSuccess;
+  if (nb > 0x7FFFFFFF || gy > 65535) return cudaErrorInvalidConfiguration;
+  const dim3 grid((unsigned)nb, (unsigned)gy);
+  switch (R) {
+    case 1: sparse_tma_kernel<1, RING><<<grid, kTmaThreads, kTmaSmemBytes, s>>>(a, err); break;
+    case 2: sparse_tma_kernel<2, RING><<<grid, kTmaThreads, kTmaSmemBytes, s>>>(a, err); break;
+    case 4: sparse_tma_kernel<4, RING><<<grid, kTmaThreads, kTmaSmemBytes, s>>>(a, err); break;
+    case 8: sparse_tma_kernel<8, RING><<<grid, kTmaThreads, kTmaSmemBytes, s>>>(a, err); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 template <bool RING>
 cudaError_t launch_sparse(int R, const SparseArgs& a, cudaStream_t s) {
   const int64_t nb = (a.M + R - 1) / R;
@@ -277,6 +310,37 @@ extern "C" rd_status rd_sparse_minplus(int R, int64_t M, const int64_t* block_st
   a.Ncols = N;
   a.min_out = min_out;
   e = launch_sparse<false>(R, a, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return RD_OK;
+}
+
+extern "C" rd_status rd_sparse_minplus_tma(int R, int64_t M, const int64_t* block_start, const uint32_t* records,
+                                           const int16_t* B, int64_t ldb, int64_t N, int16_t* C, int64_t ldc,
+                                           int32_t* min_out, int32_t* err_dev, cudaStream_t s) {
+  if (!valid_r(R) || M < 0 || N < 0 || !err_dev) return RD_ERR_ARG;
+  if (M > 0 && N > 0) {
+    if (!block_start || !records || !B || !C) return RD_ERR_ARG;
+    if (!aligned16(B) || !aligned16(C) || !aligned16(records) || ldb < N || ldb % 8 != 0 || ldc < N ||
+        ldc % 8 != 0)
+      return RD_ERR_ARG;
+  }
+  cudaError_t e = cudaSuccess;
+  if (min_out) {
+    e = launch_fill_i32(min_out, RD_INF, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (M == 0 || N == 0) return RD_OK;
+  SparseArgs a{};
+  a.M = M;
+  a.start = block_start;
+  a.rec = records;
+  a.B = B;
+  a.ldb = ldb;
+  a.C = C;
+  a.ldc = ldc;
+  a.Ncols = N;
+  a.min_out = min_out;
+  e = launch_sparse_tma<false>(R, a, err_dev, s);
   if (e != cudaSuccess) return cuda_fail(e);
   return RD_OK;
 }

@@ -493,3 +493,30 @@ def test_power_multi_equals_single_runs(rd, torch_mod, orc, graph_steps):
             o = orc.power_until_periodic(m, kmax=kmax)
             assert (r["k"], r["p"], r["q"]) == (o["k"], o["p"], o["q"]), m
     assert (res[8]["k"], res[8]["p"], res[8]["q"]) == (22, 5, 20)
+
+
+@pytest.mark.parametrize("R", [1, 2, 4, 8])
+@pytest.mark.parametrize("shape", SPARSE_SHAPES + [(300, 2000, 2500)])
+def test_sparse_minplus_tma(rd, torch_mod, orc, shape, R):
+    """The bulk-copy (cp.async.bulk + mbarrier ring) product, ragged slabs included."""
+    torch = torch_mod
+    from paper_2409_17658_gb300 import inputs
+
+    M, K, N = shape
+    a = inputs.matrix(M, K, seed=51, dist="wide")
+    keep = inputs.matrix(M, K, seed=53, dist="u32") < 3
+    a = np.where(keep, a, I16_INF).astype(np.int16)
+    b = inputs.matrix(K, N, seed=52, dist="wide")
+    A = upload(torch, a, junk=-5)
+    B = upload(torch, b, junk=-5)
+    plan = rd.sparse_plan(A, M, K, R)
+    C = torch.full((M, (N + 7) // 8 * 8), 777, dtype=torch.int16, device="cuda")
+    mn = torch.zeros(1, dtype=torch.int32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rd.sparse_minplus_tma(plan, B, C, err, N, min_out=mn)
+    assert err.item() == 0
+    want = orc.minplus_i16(a, b)
+    got = C.cpu().numpy()
+    assert np.array_equal(got[:, :N].astype(np.int32), want)
+    assert np.all(got[:, N:] == 777)
+    assert mn.item() == want.min()
