@@ -65,7 +65,30 @@ __device__ __forceinline__ void gemm_tile(const int16_t* __restrict__ Ag, const 
 
   // ---- staging helpers
   uint4 areg[2];
+  // Interior tiles (all rows and columns inside C) over whole k-tiles take the unchecked
+  // path: per-thread source pointers computed once, no per-chunk bounds arithmetic.
+  const bool full_mn = (m0 + BM <= M) && (n0 + BN <= N);
+  const int kt_full = (int)(K / BK);
+  const int16_t* a_src[2];
+  const int16_t* b_src[4];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int c = tid + h * NT;
+    a_src[h] = Ag + (m0 + (c >> 2)) * lda + (c & 3) * 8;
+  }
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const int c = tid + h * NT;
+    b_src[h] = Bg + (int64_t)(c >> 5) * ldb + n0 + (c & 31) * 8;
+  }
+  const int64_t b_step = (int64_t)BK * ldb;
+
   auto load_a_regs = [&](int kt) {
+    if (full_mn && kt < kt_full) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) areg[h] = __ldg(reinterpret_cast<const uint4*>(a_src[h] + (int64_t)kt * BK));
+      return;
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int c = tid + h * NT, row = c >> 2, kc = (c & 3) * 8;
@@ -95,6 +118,14 @@ __device__ __forceinline__ void gemm_tile(const int16_t* __restrict__ Ag, const 
   };
   auto load_b_stage = [&](int kt, int stage) {
     uint32_t* dst = Bs + stage * BS_WORDS;
+    if (full_mn && kt < kt_full) {
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int c = tid + h * NT;
+        cp_async16(dst + (c >> 5) * (BN / 2) + (c & 31) * 4, b_src[h] + (int64_t)kt * b_step);
+      }
+      return;
+    }
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       const int c = tid + h * NT, kr = c >> 5, jc = (c & 31) * 8;
