@@ -39,8 +39,8 @@ SEED_A, SEED_B = 1, 2
 SMS, DPX_LANES_PER_CLK, ADDMIN_PER_LANE, SM_MAX_MHZ = 152, 64, 2, 2070.0
 PEAK_GOPS = SMS * DPX_LANES_PER_CLK * ADDMIN_PER_LANE * SM_MAX_MHZ * 1e6 / 1e9
 # DRAM bytes (read + write) per launch of the product kernel at N = 16384, from the one-pass ncu
-# capture summarised in profiles/minplus_gemm_n16384_dram.md (8.60 GB read + 0.536 GB written).
-GEMM_TRAFFIC_BYTES = 9.136e9
+# capture summarised in profiles/minplus_gemm_n16384_dram.md (8.60 GB read + 0.552 GB written).
+GEMM_TRAFFIC_BYTES = 9.152e9
 CONFIG_NAME = "synthetic dense (min,+) GEMM N=16384, int16 uniform[0,32], P(inf)=0.5"
 
 
