@@ -18,7 +18,7 @@ namespace rd {
 namespace {
 
 constexpr int kMaxRuns = 16;
-constexpr int kMultiThreads = 64;  // product CTA width: a slab of 1024 columns
+constexpr int kMultiThreads = 128;  // product CTA width: a slab of 2048 columns
 
 struct MultiRun {
   PowerState* st;

@@ -142,7 +142,7 @@ __device__ __forceinline__ void sparse_tile_body(const SparseArgs& a, const int1
       lmin = min(lmin, __shfl_xor_sync(0xFFFFFFFFu, lmin, o));
       ldiag = min(ldiag, __shfl_xor_sync(0xFFFFFFFFu, ldiag, o));
     }
-    __shared__ int32_t red_m[4], red_d[4];
+    __shared__ int32_t red_m[8], red_d[8];
     const int warp = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
       red_m[warp] = lmin;
