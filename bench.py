@@ -42,6 +42,7 @@ PEAK_GOPS = SMS * DPX_LANES_PER_CLK * ADDMIN_PER_LANE * SM_MAX_MHZ * 1e6 / 1e9
 # capture summarised in profiles/minplus_gemm_n16384_dram.md (8.60 GB read + 0.552 GB written).
 GEMM_TRAFFIC_BYTES = 9.152e9
 CONFIG_NAME = "synthetic dense (min,+) GEMM N=16384, int16 uniform[0,32], P(inf)=0.5"
+HBM_GBS = 6652.3  # measured copy bandwidth of the GB300s (STREAM-style, read + write)
 
 
 def max_over_ranks(value_ms: float, dist, device) -> float:
@@ -234,6 +235,28 @@ def run_sparse_only(rd, torch, args) -> None:
                       "useful_addmin_gops": nnz * n / (ms * 1e-3) / 1e9,
                       "b_row_bytes_per_launch": plan["entries"] * n * 2,
                       "b_row_TBps": plan["entries"] * n * 2 / (ms * 1e-3) / 1e12}))
+
+
+def gemv_leg(rd, torch, B, n: int, reps: int = 20) -> dict:
+    """The matrix-vector form of the synthetic workload: y = x (x) B at N = 16384, against HBM bandwidth."""
+    from paper_2409_17658_gb300 import inputs
+
+    x = inputs.matrix_torch(1, n, seed=3, device="cuda")[0].contiguous()
+    y = torch.empty(n, dtype=torch.int16, device="cuda")
+    for _ in range(3):
+        rd.minplus_gemv(x, B, y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        rd.minplus_gemv(x, B, y)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nbytes = n * B.stride(0) * 2 + 2 * n * 2  # B once, x in, y out
+    return {"N": n, "ms": ms, "GB_per_s": nbytes / (ms * 1e-3) / 1e9, "bound": "hbm",
+            "frac_of_measured_hbm": nbytes / (ms * 1e-3) / 1e9 / HBM_GBS, "addmin_gops": float(n) * n / (ms * 1e-3) / 1e9,
+            "l2": "B is 512 MiB > L2; consecutive calls re-read it from HBM"}
 
 
 def batched_products(rd, torch, count: int = 64, seed: int = 4) -> dict:
@@ -509,6 +532,8 @@ def main() -> None:
     del bufs
 
     extra = {}
+    if rank == 0:
+        extra["gemv"] = gemv_leg(rd, torch, B, n)
     if rank == 0 and not args.no_serving:
         extra["serving"] = serving(rd)
     if rank == 0 and not args.no_batched:

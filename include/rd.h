@@ -116,6 +116,16 @@ rd_status rd_minplus_gemm(const int16_t *A, int64_t lda, const int16_t *B, int64
                           int64_t M, int64_t N, int64_t K, int32_t *min_out, cudaStream_t s);
 
 /*
+ * rd_minplus_gemv -- y = x (x) B, the (min,+) product of a row vector x (K
+ * entries, device, any alignment) with a K x N matrix B (ldb): y[j] =
+ * min_k x[k] + B[k][j], y device (16-byte aligned), N entries; conventions and
+ * min_out as rd_minplus_gemm.  B is read once, so this is bound by HBM
+ * bandwidth; rd_minplus_gemm uses it when M = 1.
+ */
+rd_status rd_minplus_gemv(const int16_t *x, const int16_t *B, int64_t ldb, int16_t *y, int64_t N, int64_t K,
+                          int32_t *min_out, cudaStream_t s);
+
+/*
  * rd_minplus_gemm_batched -- `count` (<= 128) independent products
  * C_i = A_i (x) B_i, each with the conventions of rd_minplus_gemm (min_out may
  * be null), in one persistent launch: two CTAs per SM walk the concatenated

@@ -55,6 +55,7 @@ def _lib():
         lib.rd_build_transfer.argtypes = [ctypes.c_int, vp, i64, vp]
         lib.rd_build_transfer_loss.argtypes = [ctypes.c_int, vp, i64, vp]
         lib.rd_minplus_gemm_batched.argtypes = [vp, ctypes.c_int, vp]
+        lib.rd_minplus_gemv.argtypes = [vp, vp, i64, vp, i64, i64, vp, vp]
         lib.rd_power_until_periodic_multi.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
         lib.rd_server_create.argtypes = [sz, ctypes.c_int, vp]
         lib.rd_server_submit.argtypes = [vp, ctypes.c_int, vp, vp, vp]
@@ -82,7 +83,7 @@ def _lib():
                      "rd_sparse_minplus", "rd_power_until_periodic_sparse", "rd_sparse_tune",
                      "rd_build_transfer_loss", "rd_minplus_gemm_batched", "rd_power_until_periodic_multi",
                      "rd_server_create", "rd_server_submit", "rd_server_wait", "rd_server_stats",
-                     "rd_server_destroy", "rd_sparse_minplus_tma"):
+                     "rd_server_destroy", "rd_sparse_minplus_tma", "rd_minplus_gemv"):
             getattr(lib, name).restype = st
         _ = i32
         _LIB = lib
@@ -164,6 +165,15 @@ def minplus_gemm(A, B, C, M: int | None = None, N: int | None = None, K: int | N
     mo = _dptr(min_out) if min_out is not None else None
     _check(_lib().rd_minplus_gemm(_dptr(A), A.stride(0), _dptr(B), B.stride(0), _dptr(C), C.stride(0), M, N, K,
                                   mo, _stream(stream)), "rd_minplus_gemm")
+
+
+def minplus_gemv(x, B, y, N: int | None = None, K: int | None = None, min_out=None, stream=None) -> None:
+    """y[:N] = x[:K] (x) B[:K, :N] (row vector times matrix) on int16 CUDA tensors."""
+    N = y.numel() if N is None else N
+    K = x.numel() if K is None else K
+    mo = _dptr(min_out) if min_out is not None else None
+    _check(_lib().rd_minplus_gemv(_dptr(x), _dptr(B), B.stride(0), _dptr(y), N, K, mo, _stream(stream)),
+           "rd_minplus_gemv")
 
 
 class GemmProblem(ctypes.Structure):

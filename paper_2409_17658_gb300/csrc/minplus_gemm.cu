@@ -327,6 +327,106 @@ __global__ void fill_min_outs_kernel(const __grid_constant__ MinOutList l) {
 
 __global__ void fill_i32_kernel(int32_t* dst, int32_t v) { *dst = v; }
 
+// ---- vector x matrix: y[j] = min_k x[k] + B[k][j] (one row of C).  Bound by HBM (B is read
+// once), so the kernel is laid out for bandwidth: a CTA owns 32 columns, held by groups of 4
+// lanes (8 columns each, one 16-byte load per row); its 128 groups split K, each streaming its
+// slice of rows with four loads in flight; x sits in shared memory (duplicated into both
+// halfwords once), and the groups' partial minima are combined in shared memory at the end.
+// N = 16384 gives 512 CTAs of 512 threads.
+constexpr int kGemvLanes = 4, kGemvCols = kGemvLanes * 8, kGemvThreads = 512;
+constexpr int kGemvGroups = kGemvThreads / kGemvLanes, kGemvXChunk = 8192, kGemvUnroll = 4;
+
+__global__ void __launch_bounds__(kGemvThreads) minplus_gemv_kernel(const int16_t* __restrict__ x,
+                                                                    const int16_t* __restrict__ B, int64_t ldb,
+                                                                    int16_t* __restrict__ y, int64_t N, int64_t K,
+                                                                    int32_t* min_out) {
+  __shared__ uint32_t xs[kGemvXChunk];
+  __shared__ uint4 part[kGemvGroups][kGemvLanes];
+  const int li = threadIdx.x % kGemvLanes, g = threadIdx.x / kGemvLanes;
+  const int64_t col = (int64_t)blockIdx.x * kGemvCols + li * 8;
+  const bool full = col + 8 <= N, any = col < N;
+  uint32_t acc[4] = {kInf2, kInf2, kInf2, kInf2};
+  for (int64_t k0 = 0; k0 < K; k0 += kGemvXChunk) {
+    const int kc = (K - k0 < kGemvXChunk) ? (int)(K - k0) : kGemvXChunk;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kc; i += blockDim.x) xs[i] = (uint32_t)(uint16_t)x[k0 + i] * 0x00010001u;
+    __syncthreads();
+    const int per = (kc + kGemvGroups - 1) / kGemvGroups;
+    const int kb = g * per, ke = (kb + per < kc) ? kb + per : kc;
+    const int16_t* bp = B + (k0 + kb) * ldb + col;
+    int k = kb;
+    if (full) {
+      for (; k + kGemvUnroll <= ke; k += kGemvUnroll, bp += kGemvUnroll * ldb) {
+        uint4 v[kGemvUnroll];
+#pragma unroll
+        for (int u = 0; u < kGemvUnroll; ++u) v[u] = __ldg(reinterpret_cast<const uint4*>(bp + u * ldb));
+#pragma unroll
+        for (int u = 0; u < kGemvUnroll; ++u) {
+          const uint32_t xw = xs[k + u];
+          acc[0] = __viaddmin_s16x2(v[u].x, xw, acc[0]);
+          acc[1] = __viaddmin_s16x2(v[u].y, xw, acc[1]);
+          acc[2] = __viaddmin_s16x2(v[u].z, xw, acc[2]);
+          acc[3] = __viaddmin_s16x2(v[u].w, xw, acc[3]);
+        }
+      }
+    }
+    for (; k < ke && any; ++k, bp += ldb) {
+      const uint32_t xw = xs[k];
+      if (full) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(bp));
+        acc[0] = __viaddmin_s16x2(v.x, xw, acc[0]);
+        acc[1] = __viaddmin_s16x2(v.y, xw, acc[1]);
+        acc[2] = __viaddmin_s16x2(v.z, xw, acc[2]);
+        acc[3] = __viaddmin_s16x2(v.w, xw, acc[3]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const uint32_t b = (col + e < N) ? (uint32_t)(uint16_t)bp[e] : (uint32_t)kInf;
+          const uint32_t sh = 16 * (e & 1);
+          const uint32_t cur = (acc[e >> 1] >> sh) & 0xFFFFu;
+          const uint32_t cand = b + (xw & 0xFFFFu);
+          const uint32_t nv = cand < cur ? cand : cur;
+          acc[e >> 1] = (acc[e >> 1] & ~(0xFFFFu << sh)) | (nv << sh);
+        }
+      }
+    }
+  }
+  part[g][li] = make_uint4(acc[0], acc[1], acc[2], acc[3]);
+  __syncthreads();
+  // tree over the groups, then the first kGemvLanes threads store
+  for (int span = kGemvGroups / 2; span > 0; span >>= 1) {
+    if (g < span) {
+      uint4 r = part[g][li];
+      const uint4 q = part[g + span][li];
+      r.x = __vmins2(r.x, q.x);
+      r.y = __vmins2(r.y, q.y);
+      r.z = __vmins2(r.z, q.z);
+      r.w = __vmins2(r.w, q.w);
+      part[g][li] = r;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < kGemvLanes) {
+    const uint4 r = part[0][li];
+    const uint32_t w4[4] = {r.x, r.y, r.z, r.w};
+    int32_t lm = kInf;
+    if (full) {
+      *reinterpret_cast<uint4*>(y + col) = r;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) lm = min(lm, (int32_t)((w4[e >> 1] >> (16 * (e & 1))) & 0xFFFF));
+    } else if (any) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (col + e < N) {
+          const int32_t v = (int32_t)((w4[e >> 1] >> (16 * (e & 1))) & 0xFFFF);
+          y[col + e] = (int16_t)v;
+          lm = min(lm, v);
+        }
+    }
+    if (min_out != nullptr && lm < kInf) atomicMin(min_out, lm);
+  }
+}
+
 template <int WHICH>  // 0 plain, 1 ring, 2 batched
 cudaError_t set_smem_attr() {
   static int done_dev[64] = {0};
@@ -391,10 +491,30 @@ extern "C" rd_status rd_minplus_gemm(const int16_t* A, int64_t lda, const int16_
     if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
   }
   if (M == 0 || N == 0) return RD_OK;
+  if (M == 1) return rd_minplus_gemv(A, B, ldb, C, N, K, min_out, s);  // one row: the bandwidth-bound kernel
   GemmParams p{};
   p.A = A; p.lda = lda; p.B = B; p.ldb = ldb; p.C = C; p.ldc = ldc;
   p.M = M; p.N = N; p.K = K; p.min_out = min_out; p.diag_out = nullptr;
   e = launch_minplus_gemm(p, false, s);
+  if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
+  return RD_OK;
+}
+
+extern "C" rd_status rd_minplus_gemv(const int16_t* x, const int16_t* B, int64_t ldb, int16_t* y, int64_t N,
+                                     int64_t K, int32_t* min_out, cudaStream_t s) {
+  if (N < 0 || K < 0) return RD_ERR_ARG;
+  if (N > 0 && (!y || (K > 0 && (!x || !B || !aligned16(B) || ldb < N || ldb % 8 != 0)))) return RD_ERR_ARG;
+  if (N > 0 && !aligned16(y)) return RD_ERR_ARG;
+  cudaError_t e = cudaSuccess;
+  if (min_out) {
+    e = launch_fill_i32(min_out, RD_INF, s);
+    if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
+  }
+  if (N == 0) return RD_OK;
+  const int64_t grid = (N + kGemvCols - 1) / kGemvCols;
+  if (grid > 0x7FFFFFFF) return RD_ERR_ARG;
+  minplus_gemv_kernel<<<(unsigned)grid, kGemvThreads, 0, s>>>(x, B, ldb, y, N, K, min_out);
+  e = cudaGetLastError();
   if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
   return RD_OK;
 }

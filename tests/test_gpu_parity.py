@@ -520,3 +520,60 @@ def test_sparse_minplus_tma(rd, torch_mod, orc, shape, R):
     assert np.array_equal(got[:, :N].astype(np.int32), want)
     assert np.all(got[:, N:] == 777)
     assert mn.item() == want.min()
+
+
+# ---------------------------------------------------------------- vector x matrix (config 3's GEMV form)
+
+@pytest.mark.parametrize("K,N", [(1, 1), (5, 13), (300, 1000), (9000, 777), (8192, 264), (20000, 2049)])
+def test_minplus_gemv(rd, torch_mod, orc, K, N):
+    torch = torch_mod
+    from paper_2409_17658_gb300 import inputs
+
+    x = inputs.matrix(1, K, seed=61, dist="wide")
+    b = inputs.matrix(K, N, seed=62, dist="wide")
+    X = torch.from_numpy(x[0].copy()).cuda()
+    B = upload(torch, b, junk=-9)
+    y = torch.full(((N + 7) // 8 * 8,), 4444, dtype=torch.int16, device="cuda")
+    mn = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rd.minplus_gemv(X, B, y, N, K, min_out=mn)
+    want = orc.minplus_i16(x, b)[0]
+    got = y.cpu().numpy()
+    assert np.array_equal(got[:N].astype(np.int32), want)
+    assert np.all(got[N:] == 4444)
+    assert mn.item() == want.min()
+    # the same through rd_minplus_gemm with M = 1
+    A = upload(torch, x)
+    C = torch.empty((1, (N + 7) // 8 * 8), dtype=torch.int16, device="cuda")
+    rd.minplus_gemm(A, B, C, 1, N, K, min_out=mn)
+    assert np.array_equal(C.cpu().numpy()[0, :N].astype(np.int32), want) and mn.item() == want.min()
+
+
+def test_minplus_gemv_full_size(rd, torch_mod, orc):
+    torch = torch_mod
+    from paper_2409_17658_gb300 import inputs
+
+    n = 16384
+    B = inputs.matrix_torch(n, n, seed=2, device="cuda")
+    x = inputs.matrix(1, n, seed=1)
+    y = torch.empty(n, dtype=torch.int16, device="cuda")
+    rd.minplus_gemv(torch.from_numpy(x[0].copy()).cuda(), B, y)
+    assert np.array_equal(y.cpu().numpy().astype(np.int32), orc.minplus_i16(x, B.cpu().numpy())[0])
+
+
+def test_minplus_gemm_n32768_sampled(rd, torch_mod, orc):
+    """The largest size of the synthetic sweep: 64 sampled entries against the oracle."""
+    torch = torch_mod
+    from paper_2409_17658_gb300 import inputs
+
+    n = 32768
+    A = inputs.matrix_torch(n, n, seed=71, dist="wide", device="cuda")
+    B = inputs.matrix_torch(n, n, seed=72, dist="wide", device="cuda")
+    C = torch.empty((n, n), dtype=torch.int16, device="cuda")
+    rd.minplus_gemm(A, B, C)
+    rng = np.random.default_rng(n)
+    ri, cj = rng.integers(0, n, 64), rng.integers(0, n, 64)
+    a_rows = A[torch.from_numpy(ri).cuda()].cpu().numpy()
+    b_cols = B[:, torch.from_numpy(cj).cuda()].cpu().numpy()
+    want = np.array([orc.minplus_i16(a_rows[e:e + 1], b_cols[:, e:e + 1])[0, 0] for e in range(64)])
+    assert np.array_equal(C[torch.from_numpy(ri).cuda(), torch.from_numpy(cj).cuda()].cpu().numpy().astype(np.int32),
+                          want)
