@@ -265,6 +265,89 @@ rd_status rd_sparse_tune(const int16_t *A, int64_t lda, int64_t N, void *scratch
                          int *best_R, float *ms_per_R, cudaStream_t s);
 
 /*
+ * Row-split power step (Sec. 4.A, Corollary 6): R = A(G) (x) B for the transfer
+ * matrix of P_m box C_n, computed from the row rules without forming A(G).  The
+ * label of an arc q -> p is the weight of p alone, and "p can follow q" is a
+ * conjunction over the rows i of "the row type of p_i is admitted by q_i" (row
+ * type = the letter, with c split by whether a vertical neighbour in p is an a).
+ * Splitting the rows after row j turns the minimum over the followers of q into
+ * two nested minima:
+ *   X[pi][sigma] = min over the row-type prefixes rho admitted by pi of
+ *                  w(p) + B[p],   p = (rho, sigma)                      (pass 1)
+ *   R[q]         = min over the row-type suffixes sigma admitted by
+ *                  q_{j+1..m} of X[q_{1..j}][sigma]                     (pass 2)
+ * with pi a correct word of j letters.  Every entry is the minimum of the same
+ * sums as A(G) (x) B, so the result is identical to rd_sparse_minplus /
+ * rd_minplus_gemm with A(G).  Both passes read and write each row once.
+ *
+ * rd_split_info_t describes a built plan (rd_split_plan fills it):
+ *   m, j     rows of the grid column and the split (rows 1..j in pass 1);
+ *   N        C_m, the order of A(G) (rows and columns of B and R);
+ *   n_rho, n_sigma  distinct row-type prefixes (rows 1..j) and suffixes
+ *            (rows j+1..m) over the C_m words: the staged rows per fiber;
+ *   n_pi, n_phi     C_j and C_{m-j}: the correct prefixes and suffixes;
+ *   list1_entries, list2_entries  admitted-list lengths (padded to 4 each);
+ *   x_rows   n_pi * n_sigma: rows of the intermediate X;
+ *   plan_bytes  device bytes of the plan;
+ *   w1, w2   column-slab widths of the two passes (32, 64 or 128); chosen
+ *            by rd_split_plan, and a caller may set another of these values
+ *            if its staged fiber fits in shared memory (else RD_ERR_ARG).
+ */
+typedef struct {
+  int32_t m, j;
+  int64_t N;
+  int32_t n_rho, n_sigma, n_pi, n_phi;
+  int64_t list1_entries, list2_entries;
+  int64_t x_rows;
+  uint64_t plan_bytes;
+  int32_t w1, w2;
+} rd_split_info_t;
+
+/* rd_split_default_j -- the split used by default, floor(m / 2); 0 when m is
+ * outside [2, RD_MAX_M] or a part would exceed 8 rows. */
+int rd_split_default_j(int m);
+
+/* rd_split_plan_bytes -- device bytes rd_split_plan needs for (m, j), from m
+ * and j alone (host arithmetic, no device work).  RD_ERR_ARG for m outside
+ * [2, RD_MAX_M], j outside [1, m-1], or a part of more than 8 rows. */
+rd_status rd_split_plan_bytes(int m, int j, size_t *bytes);
+
+/*
+ * rd_split_plan -- builds the plan for (m, j) in plan_dev (caller-owned,
+ * 256-byte aligned, at least rd_split_plan_bytes) on the GPU: the words
+ * (rd_enumerate_states), their row types, the ranks of the row-type prefixes
+ * and suffixes, the admitted lists of each pi and each phi, the fiber table
+ * [sigma][rho] -> p with w(p), and the row map [pi][phi] -> q.  Fills *info.
+ * Synchronous.  RD_ERR_ARG (bad m, j or pointer, or a fiber too large for
+ * shared memory), RD_ERR_NOMEM (plan_bytes too small), RD_ERR_RANGE (an
+ * internal count broke its bound), RD_ERR_CUDA.
+ */
+rd_status rd_split_plan(int m, int j, void *plan_dev, size_t plan_bytes, rd_split_info_t *info, cudaStream_t s);
+
+/*
+ * rd_split_minplus -- C = A(G) (x) B for the m of the plan, entries of B in
+ * [0, RD_MAX_FINITE] or RD_INF.  B (N x N, ldb), C (N x N, ldc) and the
+ * intermediate X_dev (info->x_rows x ldx int16) are caller-owned device
+ * buffers, 16-byte aligned, leading dimensions multiples of 8 and >= N; X is
+ * overwritten.  Columns N..ld-1 of C are not written.  min_out (nullable,
+ * device int32): set to min C, RD_INF if all entries are RD_INF.  Asynchronous
+ * on s.  RD_ERR_ARG for an invalid plan description or operand.
+ */
+rd_status rd_split_minplus(const rd_split_info_t *info, const void *plan_dev, const int16_t *B, int64_t ldb,
+                           int16_t *X_dev, int64_t ldx, int16_t *C, int64_t ldc, int32_t *min_out, cudaStream_t s);
+
+/*
+ * rd_power_until_periodic_split -- rd_power_until_periodic (same work buffer,
+ * outputs and errors) for A = A(G) of the plan's m, with the power step
+ * R = A (x) P_k run by the two passes of rd_split_minplus.  A_dev (N x N,
+ * lda) is read once, for the first power; X_dev as in rd_split_minplus.
+ */
+rd_status rd_power_until_periodic_split(const int16_t *A_dev, int64_t lda, const rd_split_info_t *info,
+                                        const void *plan_dev, int16_t *X_dev, int64_t ldx, int kmax, void *work_dev,
+                                        size_t work_bytes, int64_t *gamma_host, int32_t *k_out, int32_t *p_out,
+                                        int64_t *q_out, cudaStream_t s);
+
+/*
  * rd_power_until_periodic_multi -- up to 16 period searches advanced together
  * (for instance A(G) for m = 1..9).  Each run has its own operand A (dense, for
  * the first power), its block-sparse form (the same R for all runs), its own

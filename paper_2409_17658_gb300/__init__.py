@@ -77,13 +77,21 @@ def _lib():
                                                        vp, vp, vp, vp]
         lib.rd_sparse_tune.argtypes = [vp, i64, i64, vp, sz, vp, vp, vp]
         lib.rd_sparse_minplus_tma.argtypes = [ctypes.c_int, i64, vp, vp, vp, i64, i64, vp, i64, vp, vp, vp]
+        lib.rd_split_default_j.argtypes = [ctypes.c_int]
+        lib.rd_split_default_j.restype = ctypes.c_int
+        lib.rd_split_plan_bytes.argtypes = [ctypes.c_int, ctypes.c_int, vp]
+        lib.rd_split_plan.argtypes = [ctypes.c_int, ctypes.c_int, vp, sz, vp, vp]
+        lib.rd_split_minplus.argtypes = [vp, vp, vp, i64, vp, i64, vp, i64, vp, vp]
+        lib.rd_power_until_periodic_split.argtypes = [vp, i64, vp, vp, vp, i64, ctypes.c_int, vp, sz, vp, vp, vp,
+                                                      vp, vp]
         for name in ("rd_state_count", "rd_padded_dim", "rd_enumerate_states", "rd_build_transfer",
                      "rd_minplus_gemm", "rd_power_work_bytes", "rd_power_until_periodic", "rd_gamma_R",
                      "rd_power_slot", "rd_power_until_periodic_noalloc", "rd_sparse_count", "rd_sparse_build",
                      "rd_sparse_minplus", "rd_power_until_periodic_sparse", "rd_sparse_tune",
                      "rd_build_transfer_loss", "rd_minplus_gemm_batched", "rd_power_until_periodic_multi",
                      "rd_server_create", "rd_server_submit", "rd_server_wait", "rd_server_stats",
-                     "rd_server_destroy", "rd_sparse_minplus_tma", "rd_minplus_gemv"):
+                     "rd_server_destroy", "rd_sparse_minplus_tma", "rd_minplus_gemv", "rd_split_plan_bytes",
+                     "rd_split_plan", "rd_split_minplus", "rd_power_until_periodic_split"):
             getattr(lib, name).restype = st
         _ = i32
         _LIB = lib
@@ -372,6 +380,66 @@ def power_until_periodic_sparse(A, n: int, plan: dict, kmax: int, work, stream=N
                                                work.numel() * work.element_size(), ctypes.c_void_p(gamma.ctypes.data),
                                                ctypes.byref(k), ctypes.byref(p), ctypes.byref(q), _stream(stream))
     _check(st, "rd_power_until_periodic_sparse", ok=(RD_OK, RD_NOT_FOUND))
+    found = st == RD_OK
+    j = k.value + p.value if found else kmax
+    return dict(status=st, found=found, k=k.value if found else None, p=p.value if found else None,
+                q=q.value if found else None, j=j, gamma=gamma)
+
+
+class SplitInfo(ctypes.Structure):
+    """rd_split_info_t of include/rd.h."""
+    _fields_ = [("m", ctypes.c_int32), ("j", ctypes.c_int32), ("N", ctypes.c_int64), ("n_rho", ctypes.c_int32),
+                ("n_sigma", ctypes.c_int32), ("n_pi", ctypes.c_int32), ("n_phi", ctypes.c_int32),
+                ("list1_entries", ctypes.c_int64), ("list2_entries", ctypes.c_int64), ("x_rows", ctypes.c_int64),
+                ("plan_bytes", ctypes.c_uint64), ("w1", ctypes.c_int32), ("w2", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def split_default_j(m: int) -> int:
+    """The default split row of the row-split step (0 when m has none)."""
+    return _lib().rd_split_default_j(m)
+
+
+def split_plan_bytes(m: int, j: int) -> int:
+    out = ctypes.c_size_t()
+    _check(_lib().rd_split_plan_bytes(m, j, ctypes.byref(out)), "rd_split_plan_bytes")
+    return out.value
+
+
+def split_plan(m: int, j: int | None = None, device="cuda", x_ld: int | None = None, stream=None) -> dict:
+    """Allocate (torch) and build the row-split plan of A(G) for m rows, plus its intermediate X."""
+    import torch
+
+    j = split_default_j(m) if j is None else j
+    plan = torch.empty(split_plan_bytes(m, j), dtype=torch.uint8, device=device)
+    info = SplitInfo()
+    _check(_lib().rd_split_plan(m, j, _dptr(plan), plan.numel(), ctypes.byref(info), _stream(stream)),
+           "rd_split_plan")
+    ld = padded_dim(info.N) if x_ld is None else x_ld
+    X = torch.empty((info.x_rows, ld), dtype=torch.int16, device=device)
+    return dict(info=info, plan=plan, X=X)
+
+
+def split_minplus(plan: dict, B, C, min_out=None, stream=None) -> None:
+    """C[:N, :N] = A(G) (x) B[:N, :N] through the two row-split passes."""
+    mo = _dptr(min_out) if min_out is not None else None
+    X = plan["X"]
+    _check(_lib().rd_split_minplus(ctypes.byref(plan["info"]), _dptr(plan["plan"]), _dptr(B), B.stride(0), _dptr(X),
+                                   X.stride(0), _dptr(C), C.stride(0), mo, _stream(stream)), "rd_split_minplus")
+
+
+def power_until_periodic_split(A, plan: dict, kmax: int, work, stream=None) -> dict:
+    """rd_power_until_periodic with the row-split step; A is A(G) for the plan's m."""
+    gamma = np.zeros(kmax + 1, dtype=np.int64)
+    k, p, q = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    X = plan["X"]
+    st = _lib().rd_power_until_periodic_split(_dptr(A), A.stride(0), ctypes.byref(plan["info"]), _dptr(plan["plan"]),
+                                              _dptr(X), X.stride(0), kmax, _dptr(work),
+                                              work.numel() * work.element_size(), ctypes.c_void_p(gamma.ctypes.data),
+                                              ctypes.byref(k), ctypes.byref(p), ctypes.byref(q), _stream(stream))
+    _check(st, "rd_power_until_periodic_split", ok=(RD_OK, RD_NOT_FOUND))
     found = st == RD_OK
     j = k.value + p.value if found else kmax
     return dict(status=st, found=found, k=k.value if found else None, p=p.value if found else None,

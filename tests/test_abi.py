@@ -65,6 +65,15 @@ def test_argument_checks_before_any_device_work(rd):
     assert lib.rd_power_until_periodic(vp(256), 33, 40, 8, vp(256), 64, *args) == rd.RD_ERR_NOMEM
     out = ctypes.c_int64()
     assert lib.rd_gamma_R(3, 2, ctypes.byref(out)) == rd.RD_ERR_ARG  # C_n needs n >= 3
+    # row-split step: sizes come from (m, j) alone; bad splits and buffers are refused up front
+    sz = ctypes.c_size_t()
+    for m, j in ((1, 1), (10, 0), (10, 10), (16, 8), (15, 5), (3, -1)):
+        assert lib.rd_split_plan_bytes(m, j, ctypes.byref(sz)) == rd.RD_ERR_ARG, (m, j)
+    info = rd.SplitInfo()
+    assert lib.rd_split_plan(10, 5, vp(300), 1 << 30, ctypes.byref(info), None) == rd.RD_ERR_ARG
+    assert lib.rd_split_plan(10, 5, vp(256), 64, ctypes.byref(info), None) == rd.RD_ERR_NOMEM
+    assert lib.rd_split_minplus(ctypes.byref(info), vp(256), vp(256), 8, vp(256), 8, vp(256), 8, None,
+                                None) == rd.RD_ERR_ARG  # info of no built plan (m = 0)
     assert lib.rd_gamma_R(0, 5, ctypes.byref(out)) == rd.RD_ERR_ARG
 
 
@@ -78,3 +87,11 @@ def test_work_layout(rd):
     assert len(set(offs[:5])) == 5 and offs[5] == offs[0]  # P_k lives in slot k mod 5
     with pytest.raises(rd.RdError):
         rd.power_slot(n, ld, kmax, b5, 0)
+
+
+def test_split_plan_sizes(rd):
+    assert [rd.split_default_j(m) for m in (1, 2, 3, 9, 10, 15, 16)] == [0, 1, 1, 4, 5, 7, 0]
+    b = {j: rd.split_plan_bytes(10, j) for j in range(2, 9)}
+    # the plan is small next to one 64769 x 64776 int16 matrix (8.4 GB)
+    assert all(0 < v < 64 << 20 for v in b.values())
+    assert rd.split_plan_bytes(2, 1) < rd.split_plan_bytes(3, 1) < rd.split_plan_bytes(4, 2)
