@@ -151,9 +151,11 @@ def closed_form(r: dict, n: int) -> int:
 def time_to_period(rd, torch, ms: list[int], with_oracle: bool) -> dict:
     """The whole hot path for each m: build A(G), power until the first repeat, closed form for n = 3..1000.
 
-    The power step is the dense x sparse one with the rows-per-block R chosen by the
-    native autotuner (outside the timed region); at m = 9 the dense DPX step is timed
-    too, for comparison.
+    The power step is the row-split one (A(G) (x) P_k from the row rules in two passes); its plan is
+    built inside the timed region.  For comparison the dense x sparse step (rows per block R from
+    the native autotuner, outside the timed region) is timed at m >= 7, and the dense DPX step at m = 9.
+    One row-split product is also timed alone (CUDA events) against the measured HBM bandwidth:
+    it moves (2 N + 2 X rows) x N x 2 bytes (B in, X out, X in, R out).
     """
     out = {}
     for m in ms:
@@ -164,24 +166,54 @@ def time_to_period(rd, torch, ms: list[int], with_oracle: bool) -> dict:
         A = torch.empty((n, ld), dtype=torch.int16, device="cuda")
         rd.build_transfer(m, A)
         nnz = int((A[:, :n] != rd.RD_INF).sum().item())
-        R, tune_ms = rd.sparse_tune(A, n, work) if n >= 1024 else (1, {})
         # one untimed pass (first touch of allocations, module load), then the timed one
         for _ in range(2):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             rd.build_transfer(m, A)
-            plan = rd.sparse_plan(A, n, n, R)
-            r = rd.power_until_periodic_sparse(A, n, plan, kmax, work)
+            plan = rd.split_plan(m, x_ld=ld)
+            r = rd.power_until_periodic_split(A, plan, kmax, work)
             gam = [closed_form(r, nn) for nn in range(3, 1001)]
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
+            if _ == 0:
+                del plan
         products = r["j"] - 1
+        info = plan["info"]
+        C = torch.empty_like(A)
+        rd.split_minplus(plan, A, C)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            rd.split_minplus(plan, A, C)
+        e1.record()
+        torch.cuda.synchronize()
+        prod_ms = e0.elapsed_time(e1) / 3
+        moved = (2 * n + 2 * info.x_rows) * n * 2
         entry = {"N": n, "nnz_A": nnz, "k": r["k"], "p": r["p"], "q": r["q"], "products": products, "gpu_s": dt,
-                 "step": f"sparse R={R}", "tune_ms_per_product": tune_ms,
+                 "step": f"row split j={info.j} (w {info.w1}/{info.w2}, slabs per CTA {info.k1}/{info.k2})",
+                 "split_product_ms": prod_ms, "split_x_rows": info.x_rows,
+                 "split_product_GBps": moved / (prod_ms * 1e-3) / 1e9,
+                 "split_product_frac_of_measured_hbm": moved / (prod_ms * 1e-3) / 1e9 / HBM_GBS,
                  "addmin_gops": products * nnz * n / dt / 1e9,
                  "dense_equivalent_gops": products * float(n) ** 3 / dt / 1e9, "gamma_R_n3_to_12": gam[:10]}
+        del C
         if m >= 4:
             entry["remark13_holds_n5_to_1000"] = all(5 * gam[nn - 3] == 2 * (m + 1) * nn for nn in range(5, 1001, 5))
+        if m >= 7:
+            R, tune_ms = rd.sparse_tune(A, n, work)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rd.build_transfer(m, A)
+            sp = rd.sparse_plan(A, n, n, R)
+            s = rd.power_until_periodic_sparse(A, n, sp, kmax, work)
+            torch.cuda.synchronize()
+            entry["sparse_step_gpu_s"] = time.perf_counter() - t0
+            entry["sparse_R"] = R
+            entry["sparse_ms_per_product"] = tune_ms
+            entry["sparse_matches_split"] = bool(np.array_equal(s["gamma"], r["gamma"]))
+            del sp
         if m == 9:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -189,7 +221,7 @@ def time_to_period(rd, torch, ms: list[int], with_oracle: bool) -> dict:
             d = rd.power_until_periodic(A, n, kmax, work)
             torch.cuda.synchronize()
             entry["dense_step_gpu_s"] = time.perf_counter() - t0
-            entry["dense_matches_sparse"] = bool((d["k"], d["p"], d["q"]) == (r["k"], r["p"], r["q"]))
+            entry["dense_matches_split"] = bool((d["k"], d["p"], d["q"]) == (r["k"], r["p"], r["q"]))
         if with_oracle:
             import oracle
 
@@ -301,19 +333,27 @@ def batched_products(rd, torch, count: int = 64, seed: int = 4) -> dict:
     del probs, refs
     torch.cuda.empty_cache()
 
-    # A(G) for m = 1..9 powered until periodic: all together (CUDA graph of 8 steps) vs one after another
+    # A(G) for m = 1..9 powered until periodic: all together (CUDA graph of 8 steps) vs one after another;
+    # the large ones (m = 8, 9) with the row-split step, the others with the sparse step
     kmax, R = 64, 2
     runs = []
     for m in range(1, 10):
         A, n = rd.transfer_matrix(m)
-        runs.append((A, n, rd.sparse_plan(A, n, n, R), rd.power_workspace(n, A.stride(0), kmax, 8)))
+        plan = rd.split_plan(m, x_ld=A.stride(0)) if m >= 8 else rd.sparse_plan(A, n, n, R)
+        runs.append((A, n, plan, rd.power_workspace(n, A.stride(0), kmax, 8)))
+
+    def one(A, n, plan, w):
+        if "info" in plan:
+            return rd.power_until_periodic_split(A, plan, kmax, w)
+        return rd.power_until_periodic_sparse(A, n, plan, kmax, w)
+
     timings = {}
     for name in ("sequential", "together_graph"):
         for _ in range(2):  # first pass untimed
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             if name == "sequential":
-                res = [rd.power_until_periodic_sparse(A, n, plan, kmax, w) for A, n, plan, w in runs]
+                res = [one(*run) for run in runs]
             else:
                 res = rd.power_until_periodic_multi(runs, R, kmax, graph_steps=8)
             torch.cuda.synchronize()

@@ -286,12 +286,20 @@ rd_status rd_sparse_tune(const int16_t *A, int64_t lda, int64_t N, void *scratch
  *   n_rho, n_sigma  distinct row-type prefixes (rows 1..j) and suffixes
  *            (rows j+1..m) over the C_m words: the staged rows per fiber;
  *   n_pi, n_phi     C_j and C_{m-j}: the correct prefixes and suffixes;
- *   list1_entries, list2_entries  admitted-list lengths (padded to 4 each);
- *   x_rows   n_pi * n_sigma: rows of the intermediate X;
+ *   list1_entries, list2_entries  list entries of the two passes (one per
+ *            admitted slot of a fiber and output group, plus padding);
+ *   x_rows   rows of the intermediate X: the pairs (pi, sigma) for which
+ *            some word (rho, sigma) has rho admitted by pi (the others are
+ *            RD_INF and not stored);
  *   plan_bytes  device bytes of the plan;
  *   w1, w2   column-slab widths of the two passes (32, 64 or 128); chosen
  *            by rd_split_plan, and a caller may set another of these values
- *            if its staged fiber fits in shared memory (else RD_ERR_ARG).
+ *            if its staged fiber fits in shared memory (else RD_ERR_ARG);
+ *   slots1, slots2  rows staged per fiber at most (words of one sigma in
+ *            pass 1, finite rows of X of one pi in pass 2);
+ *   lmax1, lmax2    list entries of one fiber at most (staged with it);
+ *   k1, k2   column slabs one CTA sweeps per fiber (1..64, default 8; a
+ *            caller may change them like w1, w2).
  */
 typedef struct {
   int32_t m, j;
@@ -301,6 +309,9 @@ typedef struct {
   int64_t x_rows;
   uint64_t plan_bytes;
   int32_t w1, w2;
+  int32_t slots1, slots2;
+  int32_t lmax1, lmax2;
+  int32_t k1, k2;
 } rd_split_info_t;
 
 /* rd_split_default_j -- the split used by default, floor(m / 2); 0 when m is
@@ -353,8 +364,10 @@ rd_status rd_power_until_periodic_split(const int16_t *A_dev, int64_t lda, const
  * the first power), its block-sparse form (the same R for all runs), its own
  * work buffer (rd_power_work_bytes) and its own outputs, with the meaning of
  * rd_power_until_periodic_sparse; `status` receives that call's status for the
- * run.  One step of all runs is four launches (a product over every run's
- * CTAs, then normaliser/hash, finalize and compare side by side); stopped runs
+ * run.  A run may instead carry a row-split plan (split_* fields), for the step
+ * of rd_power_until_periodic_split.  One step of all runs is four launches (a
+ * product over every sparse run's CTAs -- plus two per row-split run and one
+ * per sparse run of N >= 4096 -- then normaliser/hash, finalize and compare side by side); stopped runs
  * exit at kernel entry.  graph_steps > 0 captures that many steps into one CUDA
  * graph (on a private stream ordered after s) and replays it until every run
  * has stopped; 0 launches the steps directly.  Returns RD_OK when the batch ran
@@ -373,6 +386,14 @@ typedef struct {
   int32_t k, p;        /* outputs */
   int64_t q;
   rd_status status;
+  /* Optional row-split step: with split_info non-null (a plan of
+   * rd_split_plan for this run's A(G)), the run's power step is the two passes
+   * of rd_split_minplus through split_plan and the intermediate split_X
+   * (split_info->x_rows x split_ldx), and block_start / records may be null. */
+  const rd_split_info_t *split_info;
+  const void *split_plan;
+  int16_t *split_X;
+  int64_t split_ldx;
 } rd_power_run;
 
 rd_status rd_power_until_periodic_multi(rd_power_run *runs, int count, int R, int kmax, int graph_steps,
@@ -451,9 +472,10 @@ rd_status rd_power_until_periodic_noalloc(const int16_t *A_dev, int64_t N, int64
 /*
  * rd_gamma_R -- gamma_R(P_m box C_n) for m in [1, RD_MAX_M], n >= 3 (C_n needs
  * n >= 3).  The first call for a given m builds A(G) and runs
- * rd_power_until_periodic_sparse (R = 2) on the current device, in device
- * memory this call allocates and frees (about 9 powers of C_m x C_m int16: 8 GB
- * at m = 9, 76 GB at m = 10; RD_ERR_NOMEM when that does not fit); the result (gamma for n < k + p, and (k, p, q)) is
+ * rd_power_until_periodic_split (m >= 2; m = 1 uses
+ * rd_power_until_periodic_sparse) on the current device, in device memory this
+ * call allocates and frees (about 11 powers of C_m x C_m int16: 10 GB at m = 9,
+ * 87 GB at m = 10; RD_ERR_NOMEM when that does not fit); the result (gamma for n < k + p, and (k, p, q)) is
  * cached per m for the life of the process, and later calls evaluate the
  * solution of the finite-difference equation of Prop. 7 on the host:
  * gamma(n) = gamma(k + (n - k) mod p) + q floor((n - k) / p) for n >= k.

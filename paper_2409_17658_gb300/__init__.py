@@ -210,17 +210,26 @@ class PowerRun(ctypes.Structure):
     _fields_ = [("A", ctypes.c_void_p), ("N", ctypes.c_int64), ("lda", ctypes.c_int64),
                 ("block_start", ctypes.c_void_p), ("records", ctypes.c_void_p), ("work", ctypes.c_void_p),
                 ("work_bytes", ctypes.c_size_t), ("gamma_host", ctypes.c_void_p), ("k", ctypes.c_int32),
-                ("p", ctypes.c_int32), ("q", ctypes.c_int64), ("status", ctypes.c_int)]
+                ("p", ctypes.c_int32), ("q", ctypes.c_int64), ("status", ctypes.c_int),
+                ("split_info", ctypes.c_void_p), ("split_plan", ctypes.c_void_p), ("split_X", ctypes.c_void_p),
+                ("split_ldx", ctypes.c_int64)]
 
 
 def power_until_periodic_multi(runs, R: int, kmax: int, graph_steps: int = 8, stream=None) -> list:
-    """runs: list of (A, n, plan, work).  All searches advance together; returns one result dict per run."""
+    """runs: list of (A, n, plan, work), plan from sparse_plan() (rows per block R) or split_plan().
+    All searches advance together; returns one result dict per run."""
     arr = (PowerRun * len(runs))()
     gammas = []
     for i, (A, n, plan, work) in enumerate(runs):
-        assert plan["R"] == R
         g = np.zeros(kmax + 1, dtype=np.int64)
         gammas.append(g)
+        if "info" in plan:  # row-split step
+            X = plan["X"]
+            arr[i] = PowerRun(A.data_ptr(), n, A.stride(0), None, None, work.data_ptr(),
+                              work.numel() * work.element_size(), g.ctypes.data, 0, 0, 0, 0,
+                              ctypes.addressof(plan["info"]), plan["plan"].data_ptr(), X.data_ptr(), X.stride(0))
+            continue
+        assert plan["R"] == R
         arr[i] = PowerRun(A.data_ptr(), n, A.stride(0), plan["block_start"].data_ptr(), plan["records"].data_ptr(),
                           work.data_ptr(), work.numel() * work.element_size(), g.ctypes.data, 0, 0, 0, 0)
     _check(_lib().rd_power_until_periodic_multi(arr, len(runs), R, kmax, graph_steps, _stream(stream)),
@@ -391,7 +400,9 @@ class SplitInfo(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("j", ctypes.c_int32), ("N", ctypes.c_int64), ("n_rho", ctypes.c_int32),
                 ("n_sigma", ctypes.c_int32), ("n_pi", ctypes.c_int32), ("n_phi", ctypes.c_int32),
                 ("list1_entries", ctypes.c_int64), ("list2_entries", ctypes.c_int64), ("x_rows", ctypes.c_int64),
-                ("plan_bytes", ctypes.c_uint64), ("w1", ctypes.c_int32), ("w2", ctypes.c_int32)]
+                ("plan_bytes", ctypes.c_uint64), ("w1", ctypes.c_int32), ("w2", ctypes.c_int32),
+                ("slots1", ctypes.c_int32), ("slots2", ctypes.c_int32), ("lmax1", ctypes.c_int32),
+                ("lmax2", ctypes.c_int32), ("k1", ctypes.c_int32), ("k2", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

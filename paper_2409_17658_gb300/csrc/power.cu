@@ -197,6 +197,18 @@ std::mutex g_cache_mu;
 Cached g_cache[RD_MAX_M + 1];
 constexpr int kGammaKmax = 256;
 
+rd_status finish_cached(rd_status rc, const std::vector<int64_t>& g, int32_t k, int32_t p, int64_t q, Cached* out) {
+  if (rc != RD_OK && rc != RD_NOT_FOUND) return rc;
+  out->valid = true;
+  out->found = (rc == RD_OK);
+  out->k = k;
+  out->p = p;
+  out->q = q;
+  out->j = out->found ? k + p : kGammaKmax;
+  out->gamma = g;
+  return RD_OK;
+}
+
 rd_status compute_cached(int m, Cached* out) {
   int64_t N = 0, ld = 0;
   if (rd_state_count(m, &N) != RD_OK) return RD_ERR_ARG;
@@ -219,7 +231,32 @@ rd_status compute_cached(int m, Cached* out) {
     rc = (e == cudaErrorMemoryAllocation) ? RD_ERR_NOMEM : RD_ERR_CUDA;
   }
   if (rc == RD_OK) rc = rd_build_transfer(m, A, ld, s);
-  // the dense x sparse step (A(G) is sparse, its powers are dense)
+  const int split_j = rd_split_default_j(m);
+  if (rc == RD_OK && split_j > 0) {
+    // the row-split step: A(G) (x) P_k from the row rules, in two passes
+    size_t pbytes = 0;
+    void* plan = nullptr;
+    int16_t* X = nullptr;
+    rd_split_info_t info{};
+    rc = rd_split_plan_bytes(m, split_j, &pbytes);
+    if (rc == RD_OK) e = cudaMalloc(&plan, pbytes);
+    if (rc == RD_OK && e == cudaSuccess) rc = rd_split_plan(m, split_j, plan, pbytes, &info, s);
+    if (rc == RD_OK && e == cudaSuccess) e = cudaMalloc(&X, (size_t)info.x_rows * (size_t)ld * 2);
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      rc = (e == cudaErrorMemoryAllocation) ? RD_ERR_NOMEM : RD_ERR_CUDA;
+    }
+    if (rc == RD_OK)
+      rc = rd_power_until_periodic_split(A, ld, &info, plan, X, ld, kGammaKmax, work, wbytes, g.data(), &k, &p, &q, s);
+    if (s) cudaStreamSynchronize(s);
+    if (plan) cudaFree(plan);
+    if (X) cudaFree(X);
+    if (A) cudaFree(A);
+    if (work) cudaFree(work);
+    if (s) cudaStreamDestroy(s);
+    return finish_cached(rc, g, k, p, q, out);
+  }
+  // m = 1: the dense x sparse step (A(G) is sparse, its powers are dense)
   int kR = 2;
   if (rc == RD_OK && N >= 1024) {  // small matrices: any R is a few microseconds
     int best = 0;
@@ -255,15 +292,7 @@ rd_status compute_cached(int m, Cached* out) {
   if (A) cudaFree(A);
   if (work) cudaFree(work);
   if (s) cudaStreamDestroy(s);
-  if (rc != RD_OK && rc != RD_NOT_FOUND) return rc;
-  out->valid = true;
-  out->found = (rc == RD_OK);
-  out->k = k;
-  out->p = p;
-  out->q = q;
-  out->j = out->found ? k + p : kGammaKmax;
-  out->gamma = g;
-  return RD_OK;
+  return finish_cached(rc, g, k, p, q, out);
 }
 }  // namespace
 

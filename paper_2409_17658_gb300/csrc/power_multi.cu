@@ -30,6 +30,7 @@ struct MultiRun {
   const int64_t* start;
   const uint32_t* rec;
   int64_t nb, slabs;
+  const SplitRing* split;  // non-null: this run's product is the row-split step
 };
 
 struct MultiParams {
@@ -111,6 +112,11 @@ template <int R>
 cudaError_t launch_products(const MultiParams& mp, cudaStream_t s) {
   for (int i = 0; i < mp.count; ++i) {
     const MultiRun& q = mp.r[i];
+    if (q.split != nullptr) {
+      const cudaError_t e = split_ring_product(*q.split, q.st, q.ring, q.slot_elems, q.slots, q.ld, s);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     if (q.N < kOwnLaunchN) continue;
     SparseArgs a{};
     a.M = q.N;
@@ -190,9 +196,10 @@ static void fill_params(const RunDesc* runs, int count, int R, MultiParams* mp) 
     q.A = d.A;
     q.start = d.start;
     q.rec = d.rec;
+    q.split = d.split;
     q.nb = (d.N + R - 1) / R;
     q.slabs = (d.N + kMultiThreads * 16 - 1) / (kMultiThreads * 16);
-    if (d.N < kOwnLaunchN) {
+    if (d.N < kOwnLaunchN && d.split == nullptr) {
       mp->small[mp->nsmall] = i;
       mp->cta_start[mp->nsmall + 1] = mp->cta_start[mp->nsmall] + q.nb * q.slabs;
       ++mp->nsmall;
@@ -231,6 +238,7 @@ extern "C" rd_status rd_power_until_periodic_multi(rd_power_run* runs, int count
   MultiParams mp{};
   mp.count = count;
   mp.cta_start[0] = 0;
+  SplitRing split_rings[kMaxRuns];
   int64_t maxN = 0;
   for (int i = 0; i < count; ++i) {
     rd_power_run& u = runs[i];
@@ -238,10 +246,15 @@ extern "C" rd_status rd_power_until_periodic_multi(rd_power_run* runs, int count
     u.p = 0;
     u.q = 0;
     u.status = RD_ERR_ARG;
-    if (!u.A || !u.block_start || !u.records || !u.work || !u.gamma_host) return RD_ERR_ARG;
-    if (u.N < 1 || u.lda < u.N || u.lda % 8 != 0 || !aligned16(u.A) || !aligned16(u.records) ||
+    const bool split = u.split_info != nullptr;
+    if (!u.A || !u.work || !u.gamma_host || (!split && (!u.block_start || !u.records))) return RD_ERR_ARG;
+    if (u.N < 1 || u.lda < u.N || u.lda % 8 != 0 || !aligned16(u.A) || (!split && !aligned16(u.records)) ||
         (reinterpret_cast<uintptr_t>(u.work) & 255u) != 0)
       return RD_ERR_ARG;
+    if (split) {
+      split_rings[i] = SplitRing{*u.split_info, u.split_plan, u.split_X, u.split_ldx};
+      if (!split_ring_ok(split_rings[i], u.N)) return RD_ERR_ARG;
+    }
     const size_t sb = state_bytes(kmax), pb = slot_bytes(u.N, u.lda);
     if (u.work_bytes < sb + 2 * pb) return RD_ERR_NOMEM;
     const size_t slots64 = (u.work_bytes - sb) / pb;
@@ -255,9 +268,10 @@ extern "C" rd_status rd_power_until_periodic_multi(rd_power_run* runs, int count
     q.A = u.A;
     q.start = u.block_start;
     q.rec = u.records;
+    q.split = split ? &split_rings[i] : nullptr;
     q.nb = (u.N + R - 1) / R;
     q.slabs = (u.N + kMultiThreads * 16 - 1) / (kMultiThreads * 16);
-    if (u.N < kOwnLaunchN) {
+    if (u.N < kOwnLaunchN && !split) {
       mp.small[mp.nsmall] = i;
       mp.cta_start[mp.nsmall + 1] = mp.cta_start[mp.nsmall] + q.nb * q.slabs;
       ++mp.nsmall;

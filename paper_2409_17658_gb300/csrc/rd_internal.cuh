@@ -103,6 +103,18 @@ rd_status power_search(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, v
                        ProductFn product, const void* ctx, int64_t* gamma_host, int32_t* k_out, int32_t* p_out,
                        int64_t* q_out, cudaStream_t s);
 
+// A built row-split plan with its intermediate (split.cu), and the ring-mode product it runs: the
+// next raw power R = A(G) (x) P_k into the slot of power st->k + 1, min and diag-min into st.
+struct SplitRing {
+  rd_split_info_t info;
+  const void* plan;
+  int16_t* X;
+  int64_t ldx;
+};
+bool split_ring_ok(const SplitRing& d, int64_t N);
+cudaError_t split_ring_product(const SplitRing& d, PowerState* st, int16_t* ring, int64_t slot_elems, int slots,
+                               int64_t ld, cudaStream_t s);
+
 // One period-search run as the multi-run kernels see it (power_multi.cu).
 struct RunDesc {
   PowerState* st;
@@ -114,6 +126,7 @@ struct RunDesc {
   const int64_t* start;
   const uint32_t* rec;
   int64_t nb_unused, slabs_unused;  // filled in by the launcher
+  const SplitRing* split;           // non-null: the row-split step instead of the sparse one
 };
 constexpr int kMaxRunsPerStep = 16;
 cudaError_t runs_first(const RunDesc* runs, int count, int R, int kmax, cudaStream_t s);

@@ -7,8 +7,9 @@
 //   * a query whose gamma(n) has already been produced by a running job (power
 //     n computed) is answered at once as well;
 //   * otherwise it waits on the job for its m, which is created on first need.
-// Jobs are admitted while their device footprint (A(G), its block-sparse form,
-// the work buffer) fits the HBM budget; the others wait and are admitted as
+// Jobs are admitted while their device footprint (A(G), the work buffer, and the
+// block-sparse form of A(G), or for m >= 8 the row-split plan and its
+// intermediate) fits the HBM budget; the others wait and are admitted as
 // running jobs finish and free their memory.  Every step advances ALL admitted
 // jobs together with the multi-run launches (one product launch for the small
 // ones plus one per large one, then the normaliser/finalize/compare side by
@@ -60,9 +61,12 @@ struct Job {
   int64_t* start = nullptr;
   uint32_t* rec = nullptr;
   void* work = nullptr;
+  void* plan = nullptr;       // row-split plan (large jobs)
+  int16_t* X = nullptr;       // its intermediate
+  rd::SplitRing split{};
   size_t work_bytes = 0, footprint = 0, need = 0;
   rd::RunDesc run{};
-  double cost = 1.0;  // bytes of B rows one sparse product moves: entries x N x 2
+  double cost = 1.0;  // bytes one product moves: B rows (sparse: entries x N x 2; row split: 4 (N + X rows) N)
   int k_known = 0;
   std::vector<int64_t> gamma;
   std::vector<uint64_t> waiting;
@@ -111,12 +115,52 @@ void free_job(rd_server* sv, Job* j) {
   if (j->start) cudaFree(j->start);
   if (j->rec) cudaFree(j->rec);
   if (j->work) cudaFree(j->work);
+  if (j->plan) cudaFree(j->plan);
+  if (j->X) cudaFree(j->X);
   j->A = nullptr;
   j->start = nullptr;
   j->rec = nullptr;
   j->work = nullptr;
+  j->plan = nullptr;
+  j->X = nullptr;
   sv->used -= j->footprint;
   j->footprint = 0;
+}
+
+// Large jobs (C_m >= kSplitN) step with the row-split product; smaller ones with the sparse one,
+// all of whose products share one launch.
+constexpr int64_t kSplitN = 4096;
+
+// The row-split operands of a large job: its plan and intermediate, after A and the work buffer.
+rd_status admit_split(rd_server* sv, Job* j, size_t base) {
+  const int sj = rd_split_default_j(j->m);
+  size_t pbytes = 0;
+  rd_status rc = rd_split_plan_bytes(j->m, sj, &pbytes);
+  if (rc != RD_OK) return RD_ERR_CUDA;
+  if (sv->used + pbytes > sv->budget) {
+    j->need = base + pbytes;
+    free_job(sv, j);
+    return (j->need > sv->budget) ? RD_ERR_ARG : RD_ERR_NOMEM;
+  }
+  if (cudaMalloc(&j->plan, pbytes) != cudaSuccess) return RD_ERR_CUDA;
+  j->footprint += pbytes;
+  sv->used += pbytes;
+  rc = rd_split_plan(j->m, sj, j->plan, pbytes, &j->split.info, sv->stream);
+  if (rc != RD_OK) return RD_ERR_CUDA;
+  const size_t xbytes = (size_t)j->split.info.x_rows * (size_t)j->ld * 2;
+  if (sv->used + xbytes > sv->budget) {
+    j->need = j->footprint + xbytes;  // exact now; retry when that much is free
+    free_job(sv, j);
+    return (j->need > sv->budget) ? RD_ERR_ARG : RD_ERR_NOMEM;
+  }
+  if (cudaMalloc(&j->X, xbytes) != cudaSuccess) return RD_ERR_CUDA;
+  j->footprint += xbytes;
+  sv->used += xbytes;
+  j->split.plan = j->plan;
+  j->split.X = j->X;
+  j->split.ldx = j->ld;
+  j->cost = 4.0 * (double)(j->N + j->split.info.x_rows) * (double)j->N;
+  return RD_OK;
 }
 
 // Allocate and build one job's operands; RD_OK, RD_ERR_NOMEM (does not fit now: j->need
@@ -126,28 +170,33 @@ rd_status admit(rd_server* sv, Job* j) {
   rd_padded_dim(j->N, &j->ld);
   const size_t a_bytes = (size_t)j->N * (size_t)j->ld * 2;
   rd_power_work_bytes(j->N, j->ld, sv->kmax, sv->slots, &j->work_bytes);
+  const bool use_split = j->N >= kSplitN && rd_split_default_j(j->m) > 0;
   const int64_t nb = (j->N + sv->R - 1) / sv->R;
-  const size_t start_bytes = (size_t)(nb + 1) * 8;
+  const size_t start_bytes = use_split ? 0 : (size_t)(nb + 1) * 8;
   const size_t base = a_bytes + j->work_bytes + start_bytes;
   if (j->need == 0) j->need = base;
   if (j->need > sv->budget) return RD_ERR_ARG;  // never fits: reported to its queries as RD_ERR_NOMEM
   if (sv->used + j->need > sv->budget) return RD_ERR_NOMEM;
   cudaError_t e = cudaMalloc(&j->A, a_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&j->work, j->work_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&j->start, start_bytes);
+  if (e == cudaSuccess && !use_split) e = cudaMalloc(&j->start, start_bytes);
   j->footprint = base;
   sv->used += base;
   rd_status rc = (e == cudaSuccess) ? RD_OK : RD_ERR_CUDA;
   if (rc == RD_OK) rc = rd_build_transfer(j->m, j->A, j->ld, sv->stream);
+  if (use_split && rc == RD_OK) {
+    rc = admit_split(sv, j, base);
+    if (rc == RD_ERR_NOMEM || rc == RD_ERR_ARG) return rc;  // freed already
+  }
   int64_t entries = 0;
-  if (rc == RD_OK) rc = rd_sparse_count(j->A, j->ld, j->N, j->N, sv->R, j->start, &entries, sv->stream);
-  const size_t rec_bytes = (size_t)(entries > 0 ? entries : 1) * 4 * rd_sparse_record_words(sv->R);
-  if (rc == RD_OK && sv->used + rec_bytes > sv->budget) {
+  if (!use_split && rc == RD_OK) rc = rd_sparse_count(j->A, j->ld, j->N, j->N, sv->R, j->start, &entries, sv->stream);
+  const size_t rec_bytes = use_split ? 0 : (size_t)(entries > 0 ? entries : 1) * 4 * rd_sparse_record_words(sv->R);
+  if (!use_split && rc == RD_OK && sv->used + rec_bytes > sv->budget) {
     j->need = base + rec_bytes;  // exact now; retry when that much is free
     free_job(sv, j);
     return (j->need > sv->budget) ? RD_ERR_ARG : RD_ERR_NOMEM;
   }
-  if (rc == RD_OK) {
+  if (!use_split && rc == RD_OK) {
     e = cudaMalloc(&j->rec, rec_bytes);
     if (e != cudaSuccess) rc = RD_ERR_CUDA;
     else {
@@ -155,8 +204,8 @@ rd_status admit(rd_server* sv, Job* j) {
       sv->used += rec_bytes;
     }
   }
-  if (rc == RD_OK) rc = rd_sparse_build(j->A, j->ld, j->N, j->N, sv->R, j->start, j->rec, sv->stream);
-  j->cost = 2.0 * (double)(entries > 0 ? entries : 1) * (double)j->N;
+  if (!use_split && rc == RD_OK) rc = rd_sparse_build(j->A, j->ld, j->N, j->N, sv->R, j->start, j->rec, sv->stream);
+  if (!use_split) j->cost = 2.0 * (double)(entries > 0 ? entries : 1) * (double)j->N;
   if (rc == RD_OK) {
     const size_t sb = rd::state_bytes(sv->kmax), pb = rd::slot_bytes(j->N, j->ld);
     j->run.st = reinterpret_cast<rd::PowerState*>(j->work);
@@ -169,6 +218,7 @@ rd_status admit(rd_server* sv, Job* j) {
     j->run.A = j->A;
     j->run.start = j->start;
     j->run.rec = j->rec;
+    j->run.split = use_split ? &j->split : nullptr;
     e = rd::runs_first(&j->run, 1, sv->R, sv->kmax, sv->stream);
     if (e != cudaSuccess) rc = RD_ERR_CUDA;
   }

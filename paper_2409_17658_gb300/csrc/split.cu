@@ -17,16 +17,27 @@
 //     R[q][x]         = min over sigma admitted by q_{j+1..m} of  X[q_{1..j}][sigma][x]       (pass 2)
 // for pi a correct word of j letters.  Each entry of R is the minimum of exactly the same sums as in
 // the direct product (min is exact and the weight is added once), so the result is identical.
+// Only the pairs (pi, sigma) for which some word p = (rho, sigma) has rho admitted by pi give a
+// finite row of X; X holds those rows only (about 1.28 N of them for j = m / 2).
 //
-// Cost: every row of B and every row of X is read once and written once (X has about 1.6 N rows
-// for j = m / 2), and the minima take about 36-48 N^2 operations at m = 9, 10 -- against nnz(A) N
-// add-mins over gathered rows of B in the sparse step (121 N^2 at m = 9, 206 N^2 at m = 10).
-//
-// Kernels: a CTA owns one fiber (pass 1: all p sharing sigma; pass 2: all rows of X sharing pi) and
-// a slab of W columns.  It stages the fiber's rows in shared memory (slot = rho resp. sigma rank,
-// absent rows RD_INF, plus one all-RD_INF dummy slot that pads every admitted list to a multiple
-// of four), then forms each output row as the minimum of its admitted slots with 3-input DPX
-// minima, 8 columns (one 16-byte vector) per thread.
+// Kernels: a CTA owns one fiber and a slab of W columns.  A pass-1 fiber is one sigma, its slots the
+// words p = (rho, sigma) (at most C_j of them); a pass-2 fiber is one pi, its slots the finite rows
+// X[pi][sigma].  The CTA stages the slots' row segments in shared memory (slot 0 is an all-RD_INF
+// dummy) and forms the outputs in groups of four that differ only in the letter of the boundary
+// row (row j in pass 1, row j + 1 in pass 2).  A row type t of the boundary row feeds exactly the
+// letters that admit it,
+//     a -> {a, c, d}   b -> {c}   c+ -> {a, b, c}   c- -> {a}   d -> {b, c},
+// less the letters for which the group's word, the fiber's boundary or the word itself is not
+// correct (those outputs do not exist).  So each (fiber, group) lists its admitted slots in 7
+// sub-lists keyed by that set of target letters (only 7 sets occur); a staged vector read once from shared memory
+// updates every accumulator of its set, pairs of slots with one 3-input DPX minimum per 32-bit
+// word.  Sub-lists are padded to pairs with the dummy; a thread owns 8 columns (one 16-byte vector).
+// A fiber's lists, sub-list bounds and output rows are contiguous in the plan and a few KB in size
+// for balanced splits: the CTA stages them in shared memory together with the rows, so the folding
+// loop reads nothing but shared memory.  When they do not fit (very unbalanced splits), the kernel
+// reads them from global memory instead.
+#include <mutex>
+
 #include "rd_internal.cuh"
 
 namespace rd {
@@ -36,15 +47,40 @@ constexpr int kSplitThreads = 256;
 constexpr int kSplitMaxLen = 8;  // rows per part (5^8 row-type codes, 4^8 letter codes)
 constexpr int kTauA = 0, kTauB = 1, kTauCp = 2, kTauCm = 3, kTauD = 4;
 constexpr int kTauCount = 5;
+// The sets of target letters that occur (as 4-bit masks over a, b, c, d): the letters admitting a row
+// type (acd, c, abc, a, bc) less those a neighbouring letter forbids (the correct continuations of
+// a, b, c, d are ac, cd, abcd, bcd; in pass 2 two such restrictions meet) -- {a, c, ac, bc, abc, cd,
+// acd}.  A group's record holds the starts of its 7 sub-lists and their end.
+constexpr int kSets = 7;
+constexpr int kRec = 8;
+constexpr int kDefaultSlabsPerCta = 8;
+__host__ __device__ constexpr int set_index(uint32_t mask) {
+  return mask == 0x1 ? 0 : mask == 0x4 ? 1 : mask == 0x5 ? 2 : mask == 0x6 ? 3 : mask == 0x7 ? 4 : mask == 0xC ? 5
+       : mask == 0xD ? 6 : -1;
+}
 // bit 4x + y set: the factor xy is excluded by Definition 4 (ad, da, ab, ba, bb)
 constexpr uint32_t kForbiddenPairs = (1u << (0 * 4 + 3)) | (1u << (3 * 4 + 0)) | (1u << (0 * 4 + 1)) |
                                      (1u << (1 * 4 + 0)) | (1u << (1 * 4 + 1));
-// S(letter) as a bit set over row types, for the letters a, b, c, d
-__constant__ uint8_t c_admit[4] = {
-    (1u << kTauA) | (1u << kTauCp) | (1u << kTauCm),
-    (1u << kTauD) | (1u << kTauCp),
-    (1u << kTauA) | (1u << kTauB) | (1u << kTauD) | (1u << kTauCp),
-    (1u << kTauA)};
+
+__host__ __device__ constexpr bool forbidden(int x, int y) { return (kForbiddenPairs >> (4 * x + y)) & 1u; }
+
+// S(letter) as a bit set over row types, for the letters a, b, c, d (Sec. 4.A rules)
+__host__ __device__ constexpr uint32_t admit_bits(int letter) {
+  return letter == 0   ? (1u << kTauA) | (1u << kTauCp) | (1u << kTauCm)
+         : letter == 1 ? (1u << kTauD) | (1u << kTauCp)
+         : letter == 2 ? (1u << kTauA) | (1u << kTauB) | (1u << kTauD) | (1u << kTauCp)
+                       : (1u << kTauA);
+}
+// the letters that admit row type t, as a bit set over a, b, c, d
+__host__ __device__ constexpr uint32_t targets_of(int t) {
+  uint32_t r = 0;
+  for (int l = 0; l < 4; ++l)
+    if ((admit_bits(l) >> t) & 1u) r |= 1u << l;
+  return r;
+}
+static_assert(targets_of(kTauA) == 0xDu && targets_of(kTauB) == 0x4u && targets_of(kTauCp) == 0x7u &&
+                  targets_of(kTauCm) == 0x1u && targets_of(kTauD) == 0x6u,
+              "row type -> admitting letters");
 
 // ---------------------------------------------------------------- codes
 
@@ -53,7 +89,7 @@ __host__ __device__ inline int letter_at(uint32_t code, int len, int i) { return
 
 __host__ __device__ inline bool correct_code(uint32_t code, int len) {
   for (int i = 1; i < len; ++i)
-    if ((kForbiddenPairs >> (4 * letter_at(code, len, i) + letter_at(code, len, i + 1))) & 1u) return false;
+    if (forbidden(letter_at(code, len, i), letter_at(code, len, i + 1))) return false;
   return true;
 }
 
@@ -81,7 +117,7 @@ __device__ inline bool admits(uint32_t w, uint32_t t, int len) {
   for (int i = len; i >= 1; --i) {
     const uint32_t ty = t % kTauCount;
     t /= kTauCount;
-    if (!((c_admit[letter_at(w, len, i)] >> ty) & 1u)) return false;
+    if (!((admit_bits(letter_at(w, len, i)) >> ty) & 1u)) return false;
   }
   return true;
 }
@@ -94,45 +130,46 @@ __host__ __device__ inline int64_t ipow(int64_t b, int e) {
 
 // ---------------------------------------------------------------- plan layout
 
-// Host-side bound on the distinct row-type strings of `len` rows: each is a correct word of len
-// letters with every c marked + or -.
-int64_t type_bound(int len) {
+// Host-side bound on the distinct row-type strings of a part of `len` rows: each is a correct word
+// of len letters with its c's marked + or -, and only a c in the boundary row (the last row of
+// pass 1's part, the first of pass 2's) has a vertical neighbour outside the part; every other mark
+// is fixed by the word.
+int64_t type_bound(int len, bool boundary_last) {
   int64_t t = 0;
   for (uint32_t c = 0; c < (1u << (2 * len)); ++c) {
     if (!correct_code(c, len)) continue;
-    int64_t v = 1;
-    for (int i = 1; i <= len; ++i)
-      if (letter_at(c, len, i) == 2) v *= 2;
-    t += v;
+    t += letter_at(c, len, boundary_last ? len : 1) == 2 ? 2 : 1;
   }
   return t;
 }
 
-// Host-side bound on the padded admitted-list entries of the correct words of `len` letters: a word
-// admits at most prod_i |S(w_i)| row-type strings (|S| = 3, 2, 4, 1 for a, b, c, d) and at most
-// `types` of them exist.
-int64_t list_bound(int len, int64_t types) {
+// Host-side bound on the list entries of one fiber over all groups of a part of len rows: a group
+// word w of len - 1 letters admits at most prod_i |S(w_i)| strings of its rows (|S| = 3, 2, 4, 1 for
+// a, b, c, d), each with one of 5 boundary types, and the fiber has at most `slots` slots; each of
+// the 7 sub-lists adds at most one padding entry.
+int64_t fiber_list_bound(int len, int64_t slots) {
   const int64_t admit_size[4] = {3, 2, 4, 1};
   int64_t t = 0;
-  for (uint32_t c = 0; c < (1u << (2 * len)); ++c) {
-    if (!correct_code(c, len)) continue;
-    int64_t v = 1;
-    for (int i = 1; i <= len; ++i) v *= admit_size[letter_at(c, len, i)];
-    t += ((v < types ? v : types) + 3) & ~3ll;
+  for (uint32_t c = 0; c < (1u << (2 * (len - 1))); ++c) {
+    if (!correct_code(c, len - 1)) continue;
+    int64_t v = kTauCount;
+    for (int i = 1; i <= len - 1; ++i) v *= admit_size[letter_at(c, len - 1, i)];
+    t += (v < slots ? v : slots) + kSets;
   }
   return t;
 }
 
 int64_t correct_count(int len) {
+  if (len == 0) return 1;  // the empty word
   int64_t n = 0;
   return rd_state_count(len, &n) == RD_OK ? n : -1;
 }
 
 struct Layout {
   int m, j, h;
-  int64_t N, nPi, nPhi, rhoB, sigB, c1B, c2B;
-  size_t totals, codes, wts, rankR, rankS, rankPi, rankPhi, rhoCode, sigCode, piCode, phiCode, c1s, c2s, c1, c2, fiber,
-      outrow, bytes;
+  int64_t N, nPi, nPhi, nG1, nG2, rhoB, sigB, l1B, l2B;
+  size_t codes, wts, rankR, rankS, rankPi, rankPhi, rankG1, rankG2, rhoCode, sigCode, piCode, g1Code, g2Code, fiber,
+      outrow, fstart1, fmem1, frho1, xrank, xsig, fstart2, gls1, l1, go1, gls2, l2, go2, counters, bytes;
 };
 
 bool make_layout(int m, int j, Layout* L) {
@@ -145,33 +182,48 @@ bool make_layout(int m, int j, Layout* L) {
   L->N = correct_count(m);
   L->nPi = correct_count(j);
   L->nPhi = correct_count(h);
-  L->rhoB = type_bound(j);
-  L->sigB = type_bound(h);
-  L->c1B = list_bound(j, L->rhoB);
-  L->c2B = list_bound(h, L->sigB);
+  L->nG1 = correct_count(j - 1);
+  L->nG2 = correct_count(h - 1);
+  L->rhoB = type_bound(j, true);
+  L->sigB = type_bound(h, false);
+  // a pass-1 fiber has at most C_j slots (rho and sigma fix the letters), a pass-2 fiber at most n_sigma
+  L->l1B = L->sigB * fiber_list_bound(j, L->nPi);
+  L->l2B = L->nPi * fiber_list_bound(h, L->sigB);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
     off = round_up(off + bytes, 256);
     return o;
   };
-  L->totals = take(16 * 4);
+  const size_t xcap = (size_t)L->nPi * (size_t)L->sigB;
   L->codes = take((size_t)L->N * 4);
   L->wts = take((size_t)L->N);
   L->rankR = take((size_t)(ipow(kTauCount, j) + 1) * 4);
   L->rankS = take((size_t)(ipow(kTauCount, h) + 1) * 4);
   L->rankPi = take((size_t)(ipow(4, j) + 1) * 4);
   L->rankPhi = take((size_t)(ipow(4, h) + 1) * 4);
+  L->rankG1 = take((size_t)(ipow(4, j - 1) + 1) * 4);
+  L->rankG2 = take((size_t)(ipow(4, h - 1) + 1) * 4);
   L->rhoCode = take((size_t)L->rhoB * 4);
   L->sigCode = take((size_t)L->sigB * 4);
   L->piCode = take((size_t)L->nPi * 4);
-  L->phiCode = take((size_t)L->nPhi * 4);
-  L->c1s = take((size_t)(L->nPi + 1) * 4);
-  L->c2s = take((size_t)(L->nPhi + 1) * 4);
-  L->c1 = take((size_t)L->c1B * 2);
-  L->c2 = take((size_t)L->c2B * 2);
+  L->g1Code = take((size_t)L->nG1 * 4);
+  L->g2Code = take((size_t)L->nG2 * 4);
   L->fiber = take((size_t)L->sigB * (size_t)L->rhoB * 4);
   L->outrow = take((size_t)L->nPi * (size_t)L->nPhi * 4);
+  L->fstart1 = take((size_t)(L->sigB + 1) * 4);
+  L->fmem1 = take((size_t)L->N * 4);
+  L->frho1 = take((size_t)L->N * 4);
+  L->xrank = take((xcap + 1) * 4);
+  L->xsig = take(xcap * 4);
+  L->fstart2 = take((size_t)(L->nPi + 1) * 4);
+  L->gls1 = take(((size_t)L->sigB * (size_t)L->nG1 * kRec + 1) * 4);
+  L->l1 = take((size_t)L->l1B * 2);
+  L->go1 = take((size_t)L->sigB * (size_t)L->nG1 * 4 * 4);
+  L->gls2 = take(((size_t)L->nPi * (size_t)L->nG2 * kRec + 1) * 4);
+  L->l2 = take((size_t)L->l2B * 2);
+  L->go2 = take((size_t)L->nPi * (size_t)L->nG2 * 4 * 4);
+  L->counters = take(8 * 4);
   L->bytes = off;
   return true;
 }
@@ -185,11 +237,14 @@ const T* at(const void* base, size_t off) {
   return reinterpret_cast<const T*>(static_cast<const char*>(base) + off);
 }
 
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
 // ---------------------------------------------------------------- plan kernels
 
 // Each correct word of length m marks the row-type codes of its first j rows and of the rest.
 __global__ void split_mark_kernel(const uint32_t* codes, int64_t N, int m, int j, int32_t* flagR, int32_t* flagS) {
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+  GRID_STRIDE(p, N) {
     const uint32_t code = codes[p];
     uint32_t rc = 0, sc = 0;
     for (int i = 1; i <= j; ++i) rc = rc * kTauCount + row_type(code, m, i);
@@ -200,8 +255,7 @@ __global__ void split_mark_kernel(const uint32_t* codes, int64_t N, int m, int j
 }
 
 __global__ void correct_flag_kernel(int32_t* flags, int len, int64_t n) {
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
-    flags[c] = correct_code((uint32_t)c, len) ? 1 : 0;
+  GRID_STRIDE(c, n) flags[c] = correct_code((uint32_t)c, len) ? 1 : 0;
 }
 
 // In-place exclusive scan of v[0..n) with the total written to v[n]; one CTA.
@@ -243,29 +297,8 @@ __global__ void scan_i32_kernel(int32_t* v, int64_t n) {
 
 // inv[rank[c]] = c for every present code c (rank is an exclusive scan of presence flags).
 __global__ void invert_kernel(const int32_t* rank, int64_t n, int32_t* inv) {
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+  GRID_STRIDE(c, n) {
     if (rank[c + 1] > rank[c]) inv[rank[c]] = (int32_t)c;
-}
-
-// Admitted lists: for each letter word w (n_w of them, len letters), the row-type strings t among
-// the n_t present ones that it admits, in increasing code order, padded with the dummy slot n_t to a
-// multiple of four.  count: cnt[w] = padded length; fill: the entries from start[w].
-__global__ void list_count_kernel(const int32_t* wcode, int64_t n_w, const int32_t* tcode, int64_t n_t, int len,
-                                  int32_t* cnt) {
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_w; w += (int64_t)gridDim.x * blockDim.x) {
-    int32_t c = 0;
-    for (int64_t t = 0; t < n_t; ++t) c += admits((uint32_t)wcode[w], (uint32_t)tcode[t], len) ? 1 : 0;
-    cnt[w] = (c + 3) & ~3;
-  }
-}
-
-__global__ void list_fill_kernel(const int32_t* wcode, int64_t n_w, const int32_t* tcode, int64_t n_t, int len,
-                                 const int32_t* start, uint16_t* lst) {
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_w; w += (int64_t)gridDim.x * blockDim.x) {
-    int32_t e = start[w];
-    for (int64_t t = 0; t < n_t; ++t)
-      if (admits((uint32_t)wcode[w], (uint32_t)tcode[t], len)) lst[e++] = (uint16_t)t;
-    while (e < start[w + 1]) lst[e++] = (uint16_t)n_t;
   }
 }
 
@@ -274,7 +307,7 @@ __global__ void split_index_kernel(const uint32_t* codes, int64_t N, int m, int 
                                    const int32_t* rankS, int64_t n_rho, const int32_t* rankPi,
                                    const int32_t* rankPhi, int64_t n_phi, int32_t* fiber, int32_t* outrow) {
   const int h = m - j;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+  GRID_STRIDE(p, N) {
     const uint32_t code = codes[p];
     uint32_t rc = 0, sc = 0;
     for (int i = 1; i <= j; ++i) rc = rc * kTauCount + row_type(code, m, i);
@@ -282,6 +315,155 @@ __global__ void split_index_kernel(const uint32_t* codes, int64_t N, int m, int 
     fiber[(int64_t)rankS[sc] * n_rho + rankR[rc]] = (int32_t)(p * 32 + word_weight_of(code, m));
     const uint32_t pi = code >> (2 * h), phi = code & ((1u << (2 * h)) - 1u);
     outrow[(int64_t)rankPi[pi] * n_phi + rankPhi[phi]] = (int32_t)p;
+  }
+}
+
+// Pass-1 fibers in compact form: the words of fiber sigma in increasing rho rank.
+__global__ void fiber_count_kernel(const int32_t* fiber, int64_t n_sigma, int64_t n_rho, int32_t* cnt) {
+  GRID_STRIDE(s, n_sigma) {
+    int32_t c = 0;
+    for (int64_t r = 0; r < n_rho; ++r) c += fiber[s * n_rho + r] >= 0 ? 1 : 0;
+    cnt[s] = c;
+  }
+}
+
+__global__ void fiber_fill_kernel(const int32_t* fiber, int64_t n_sigma, int64_t n_rho, const int32_t* start,
+                                  int32_t* mem, int32_t* rho_of, int32_t* max_slots) {
+  GRID_STRIDE(s, n_sigma) {
+    int32_t e = start[s];
+    for (int64_t r = 0; r < n_rho; ++r) {
+      const int32_t v = fiber[s * n_rho + r];
+      if (v < 0) continue;
+      mem[e] = v;
+      rho_of[e] = (int32_t)r;
+      ++e;
+    }
+    atomicMax(max_slots, e - start[s]);
+  }
+}
+
+// xflag[pi][sigma] = 1 when some word of fiber sigma has its rho admitted by pi (a finite row of X).
+__global__ void xflag_kernel(const int32_t* piCode, int64_t n_pi, int64_t n_sigma, const int32_t* fstart1,
+                             const int32_t* frho1, const int32_t* rhoCode, int j, int32_t* xflag) {
+  GRID_STRIDE(i, n_pi * n_sigma) {
+    const int64_t pi = i / n_sigma, s = i % n_sigma;
+    int32_t fin = 0;
+    for (int32_t e = fstart1[s]; e < fstart1[s + 1] && !fin; ++e)
+      fin = admits((uint32_t)piCode[pi], (uint32_t)rhoCode[frho1[e]], j) ? 1 : 0;
+    xflag[i] = fin;
+  }
+}
+
+// The sigma of each finite row of X, and the pass-2 fiber starts (X rows of pi are contiguous).
+__global__ void xsig_kernel(const int32_t* xrank, int64_t n_pi, int64_t n_sigma, int32_t* xsig, int32_t* fstart2,
+                            int32_t* max_slots) {
+  GRID_STRIDE(i, n_pi * n_sigma) {
+    if (xrank[i + 1] > xrank[i]) xsig[xrank[i]] = (int32_t)(i % n_sigma);
+    if (i % n_sigma == 0) {
+      const int64_t pi = i / n_sigma;
+      fstart2[pi] = xrank[i];
+      atomicMax(max_slots, xrank[i + n_sigma] - xrank[i]);
+      if (pi == n_pi - 1) fstart2[n_pi] = xrank[n_pi * n_sigma];
+    }
+  }
+}
+
+// One (fiber, group) of a pass: enumerate its slots, and for each slot admitted on the group's rows
+// give the set of target letters (the letters admitting the boundary type that give an existing
+// output).  FILL = false counts entries per set (each padded to even) into cnt[8 (f G + g) + set]
+// (entry 7 stays 0, so after the scan it is the record's end) and raises *bad for a set outside the
+// 7; FILL = true writes the 1-based slot numbers from start and pads with the dummy slot 0.
+struct GroupArgs {
+  int first;  // 1: pass 1 (boundary = last row of the part), 0: pass 2 (boundary = first row)
+  int len;    // rows of the part (j resp. h)
+  int64_t n_fibers, n_groups;
+  const int32_t* gcode;    // group words (len - 1 letters)
+  const int32_t* fstart;   // slot ranges of the fibers (pass 1: into frho; pass 2: X rows)
+  const int32_t* slot_tc;  // pass 1: rho rank of each member; pass 2: sigma rank of each X row
+  const int32_t* tcode;    // row-type code of a rho / sigma rank
+  const int32_t* piCode;   // pass 2: the fiber's word pi (its last letter borders the part)
+};
+
+__device__ inline uint32_t allowed_letters(const GroupArgs& a, int64_t f, uint32_t gw) {
+  const int glen = a.len - 1;
+  uint32_t allow = 0;
+  for (int l = 0; l < 4; ++l) {
+    bool ok;
+    if (a.first)
+      ok = glen == 0 || !forbidden(letter_at(gw, glen, glen), l);
+    else
+      ok = (glen == 0 || !forbidden(l, letter_at(gw, glen, 1))) && !forbidden((int)(a.piCode[f] & 3), l);
+    if (ok) allow |= 1u << l;
+  }
+  return allow;
+}
+
+template <bool FILL>
+__global__ void group_lists_kernel(GroupArgs a, int32_t* cnt_or_start, uint16_t* lst, int32_t* bad) {
+  GRID_STRIDE(i, a.n_fibers * a.n_groups) {
+    const int64_t f = i / a.n_groups, g = i % a.n_groups;
+    const uint32_t gw = (uint32_t)a.gcode[g];
+    const int glen = a.len - 1;
+    const uint32_t allow = allowed_letters(a, f, gw);
+    int32_t pos[kRec];
+    for (int s = 0; s < kRec; ++s) pos[s] = FILL ? cnt_or_start[i * kRec + s] : 0;
+    const uint32_t p = (uint32_t)ipow(kTauCount, glen);
+    for (int32_t e = a.fstart[f]; e < a.fstart[f + 1]; ++e) {
+      const uint32_t tc = (uint32_t)a.tcode[a.slot_tc[e]];
+      const int t = a.first ? (int)(tc % kTauCount) : (int)(tc / p);
+      const uint32_t rest = a.first ? tc / kTauCount : tc % p;
+      if (!admits(gw, rest, glen)) continue;
+      const uint32_t set = targets_of(t) & allow;
+      if (set == 0) continue;
+      const int si = set_index(set);
+      if (si < 0) {
+        if (!FILL) atomicExch(bad, 1);
+        continue;
+      }
+      if (FILL)
+        lst[pos[si]++] = (uint16_t)(e - a.fstart[f] + 1);
+      else
+        ++pos[si];
+    }
+    if (FILL) {
+      for (int s = 0; s < kSets; ++s)
+        if (pos[s] & 1) lst[pos[s]] = 0;
+    } else {
+      for (int s = 0; s < kSets; ++s) cnt_or_start[i * kRec + s] = (pos[s] + 1) & ~1;
+      cnt_or_start[i * kRec + kSets] = 0;
+    }
+  }
+}
+
+// The list entries of each fiber (its records are contiguous), maximum into *out.
+__global__ void fiber_list_max_kernel(const int32_t* gls, int64_t n_fibers, int64_t n_groups, int32_t* out) {
+  GRID_STRIDE(f, n_fibers) {
+    atomicMax(out, gls[(f + 1) * n_groups * kRec] - gls[f * n_groups * kRec]);
+  }
+}
+
+// Output rows of the groups: go[4 (f G + g) + l] = the row written for letter l at the boundary,
+// or -1.  Pass 1: the X row of (pi = group + l, sigma = f) when it is finite (a step of xrank).
+// Pass 2: the row q of R of the word pi_f + (l + group) when that word is correct.
+__global__ void group_out_kernel(GroupArgs a, const int32_t* rank_w, const int32_t* xrank, int64_t n_sigma,
+                                 const int32_t* outrow, int64_t n_phi, int32_t* go) {
+  GRID_STRIDE(i, a.n_fibers * a.n_groups) {
+    const int64_t f = i / a.n_groups, g = i % a.n_groups;
+    const uint32_t gw = (uint32_t)a.gcode[g];
+    const int glen = a.len - 1;
+    const uint32_t allow = allowed_letters(a, f, gw);
+    for (int l = 0; l < 4; ++l) {
+      int32_t row = -1;
+      if ((allow >> l) & 1u) {
+        if (a.first) {
+          const int64_t x = (int64_t)rank_w[(gw << 2) | (uint32_t)l] * n_sigma + f;
+          if (xrank[x + 1] > xrank[x]) row = xrank[x];
+        } else {
+          row = outrow[f * n_phi + rank_w[((uint32_t)l << (2 * glen)) | gw]];
+        }
+      }
+      go[i * 4 + l] = row;
+    }
   }
 }
 
@@ -293,13 +475,15 @@ struct SplitPass {
   int16_t* out;  // pass 1: X;  pass 2: R
   int64_t ldout;
   int64_t ncols;
-  int32_t n_slots;  // rows staged per fiber (rho resp. sigma ranks); slot n_slots is the dummy
-  int32_t n_out;    // output rows per fiber (pi resp. phi ranks)
-  int32_t n_sigma;
-  const int32_t* src;     // pass 1: [sigma][rho] = p * 32 + w(p), or -1
-  const int32_t* start;   // [n_out + 1] admitted-list starts (multiples of 4)
-  const uint16_t* lst;    // admitted slots
-  const int32_t* dst;     // pass 2: [pi][phi] = row q of R, or -1
+  int32_t n_groups;
+  int32_t max_slots;      // shared-memory rows = max_slots + 1 (row 0 is the dummy)
+  int32_t max_list;       // list entries of one fiber at most
+  int32_t slabs_per_cta;  // column slabs one CTA sweeps with its fiber staged once
+  const int32_t* fstart;  // [fibers + 1] slot ranges: pass 1 into fmem, pass 2 X rows
+  const int32_t* fmem;    // pass 1: p * 32 + w(p) per slot
+  const int32_t* gls;     // [8 (fibers G) + 1] per (fiber, group): the 7 sub-list starts (even), then the end
+  const uint16_t* lst;    // 1-based slot numbers, 0 = dummy
+  const int32_t* go;      // [(fibers G) * 4] output rows per boundary letter, or -1
   int32_t* min_out;
   int32_t* diag_out;
   PowerState* st;  // ring mode: B = power slot k (pass 1), R = slot k + 1 (pass 2)
@@ -310,11 +494,62 @@ struct SplitPass {
 
 __device__ __forceinline__ uint32_t min3(uint32_t a, uint32_t b, uint32_t c) { return __vimin3_s16x2(a, b, c); }
 
-template <int W, bool FIRST, bool RING>
+template <int SET>
+__device__ __forceinline__ void fold_pair(uint4 (&acc)[4], const uint4& v0, const uint4& v1) {
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    if ((SET >> l) & 1) {
+      acc[l].x = min3(acc[l].x, v0.x, v1.x);
+      acc[l].y = min3(acc[l].y, v0.y, v1.y);
+      acc[l].z = min3(acc[l].z, v0.z, v1.z);
+      acc[l].w = min3(acc[l].w, v0.w, v1.w);
+    }
+  }
+}
+
+// Folds the sub-list [e0, e1) (even bounds) of target set SET into the group's accumulators.
+template <int SET, int LR>
+__device__ __forceinline__ void fold_sublist(uint4 (&acc)[4], const uint4* sm, const uint32_t* pairs, int e0, int e1,
+                                             int lane) {
+  int p = e0 >> 1;
+  const int pe = e1 >> 1;
+  for (; p + 2 <= pe; p += 2) {
+    const uint32_t i0 = pairs[p], i1 = pairs[p + 1];
+    const uint4 v0 = sm[(int)(i0 & 0xFFFFu) * LR + lane];
+    const uint4 v1 = sm[(int)(i0 >> 16) * LR + lane];
+    const uint4 v2 = sm[(int)(i1 & 0xFFFFu) * LR + lane];
+    const uint4 v3 = sm[(int)(i1 >> 16) * LR + lane];
+    fold_pair<SET>(acc, v0, v1);
+    fold_pair<SET>(acc, v2, v3);
+  }
+  if (p < pe) {
+    const uint32_t i0 = pairs[p];
+    fold_pair<SET>(acc, sm[(int)(i0 & 0xFFFFu) * LR + lane], sm[(int)(i0 >> 16) * LR + lane]);
+  }
+}
+
+// Shared memory of one CTA: the staged rows, then the fiber's sub-list bounds (uint16, local to the
+// fiber's list), its output rows (int32), its list (uint16) and its words (pass 1, int32), each part
+// 16-byte aligned.
+struct PassSmem {
+  size_t gls, go, lst, mem, bytes;
+};
+__host__ __device__ inline PassSmem pass_smem_layout(int max_slots, int n_groups, int max_list, int W) {
+  PassSmem p;
+  const size_t data = (size_t)(max_slots + 1) * (size_t)W * 2;
+  p.gls = data;
+  p.go = p.gls + (size_t)n_groups * kRec * 2;
+  p.lst = p.go + (size_t)n_groups * 4 * 4;
+  p.mem = p.lst + ((size_t)max_list * 2 + 15) / 16 * 16;
+  p.bytes = p.mem + ((size_t)max_slots * 4 + 15) / 16 * 16;
+  return p;
+}
+
+template <int W, bool FIRST, bool RING, bool STAGED>
 __global__ void __launch_bounds__(kSplitThreads) split_pass_kernel(SplitPass a) {
   extern __shared__ uint4 sm[];
-  constexpr int LR = W / 8;                 // threads per row of the slab
-  constexpr int G = kSplitThreads / LR;     // rows handled side by side
+  constexpr int LR = W / 8;              // threads per row of the slab
+  constexpr int G = kSplitThreads / LR;  // groups (resp. staged rows) handled side by side
   const int16_t* in = a.in;
   int16_t* out = a.out;
   if (RING) {
@@ -325,89 +560,136 @@ __global__ void __launch_bounds__(kSplitThreads) split_pass_kernel(SplitPass a) 
     else
       out = a.ring + (int64_t)((k + 1) % a.slots) * a.slot_elems;
   }
-  const int lane = threadIdx.x % LR, g = threadIdx.x / LR;
+  const int lane = threadIdx.x % LR, gi = threadIdx.x / LR;
   const int64_t f = blockIdx.y;
-  const int64_t c = (int64_t)blockIdx.x * W + lane * 8;
-  const bool ok = c < a.ncols;
   const uint4 inf4 = make_uint4(kInf2, kInf2, kInf2, kInf2);
 
-  // stage the fiber: slots 0..n_slots (the last one is the RD_INF dummy)
-  const int nst = a.n_slots + 1;
-  for (int s0 = g; s0 < nst; s0 += 4 * G) {
-    uint4 v[4];
+  // stage the fiber's metadata once: sub-list bounds relative to the fiber's first list entry,
+  // output rows, the list itself (its bounds are even, so it moves as 32-bit pairs) and, in pass 1,
+  // the words of the fiber
+  const PassSmem lay = pass_smem_layout(a.max_slots, a.n_groups, a.max_list, W);
+  char* smb = reinterpret_cast<char*>(sm);
+  uint16_t* sgls = reinterpret_cast<uint16_t*>(smb + lay.gls);
+  int4* sgo = reinterpret_cast<int4*>(smb + lay.go);
+  uint32_t* slst = reinterpret_cast<uint32_t*>(smb + lay.lst);
+  int32_t* smem_words = reinterpret_cast<int32_t*>(smb + lay.mem);
+  const int64_t r0 = f * a.n_groups * kRec;
+  const int32_t base = __ldg(a.gls + r0);
+  const int4* go4 = reinterpret_cast<const int4*>(a.go) + f * a.n_groups;
+  const uint32_t* glst = reinterpret_cast<const uint32_t*>(a.lst) + (base >> 1);
+  const int32_t f0 = __ldg(a.fstart + f);
+  const int nst = __ldg(a.fstart + f + 1) - f0 + 1;  // row 0 is the dummy, rows 1..n the slots
+  if (STAGED) {
+    const int nb = a.n_groups * kRec;
+    for (int i = threadIdx.x; i < nb; i += kSplitThreads) sgls[i] = (uint16_t)(__ldg(a.gls + r0 + i) - base);
+    for (int i = threadIdx.x; i < a.n_groups; i += kSplitThreads) sgo[i] = __ldg(go4 + i);
+    const int npairs = (__ldg(a.gls + r0 + nb) - base) >> 1;
+    for (int i = threadIdx.x; i < npairs; i += kSplitThreads) slst[i] = __ldg(glst + i);
+    if (FIRST)
+      for (int i = threadIdx.x; i < nst - 1; i += kSplitThreads) smem_words[i] = __ldg(a.fmem + f0 + i);
+  }
+  const uint32_t* pairs = STAGED ? slst : glst;
+  int32_t lmin = kInf, ldiag = kInf;
+  uint32_t m2 = kInf2;  // halfword minima of the full vectors written (pass 2)
+
+  const int64_t slabs = (a.ncols + W - 1) / W;
+  const int64_t sb_end = min(slabs, (int64_t)(blockIdx.x + 1) * a.slabs_per_cta);
+  for (int64_t sb = (int64_t)blockIdx.x * a.slabs_per_cta; sb < sb_end; ++sb) {
+    const int64_t c = sb * W + lane * 8;
+    const bool ok = c < a.ncols;
+    __syncthreads();  // the metadata is staged / the previous slab has been consumed
+    for (int s0 = gi; s0 < nst; s0 += 4 * G) {
+      int32_t e[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int s = s0 + u * G;
-      v[u] = inf4;
-      if (s < a.n_slots && ok) {
-        if (FIRST) {
-          const int32_t e = __ldg(a.src + f * a.n_slots + s);
-          if (e >= 0) {
-            const uint4 x = __ldg(reinterpret_cast<const uint4*>(in + (int64_t)(e >> 5) * a.ldin + c));
-            const uint32_t w2 = (uint32_t)(e & 31) * 0x00010001u;
-            v[u] = make_uint4(__viaddmin_s16x2(x.x, w2, kInf2), __viaddmin_s16x2(x.y, w2, kInf2),
-                              __viaddmin_s16x2(x.z, w2, kInf2), __viaddmin_s16x2(x.w, w2, kInf2));
-          }
-        } else {
-          v[u] = __ldg(reinterpret_cast<const uint4*>(in + (f * a.n_sigma + s) * a.ldin + c));
+      for (int u = 0; u < 4; ++u) {
+        const int s = s0 + u * G;
+        e[u] = -1;
+        if (s >= 1 && s < nst) {
+          if (FIRST)
+            e[u] = STAGED ? smem_words[s - 1] : __ldg(a.fmem + f0 + s - 1);
+          else
+            e[u] = f0 + s - 1;
         }
       }
-    }
+      uint4 v[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int s = s0 + u * G;
-      if (s < nst) sm[s * LR + lane] = v[u];
-    }
-  }
-  __syncthreads();
-
-  int32_t lmin = kInf, ldiag = kInf;
-  for (int o = g; o < a.n_out; o += G) {
-    int64_t row;
-    if (FIRST) {
-      row = (int64_t)o * a.n_sigma + f;
-    } else {
-      row = __ldg(a.dst + f * a.n_out + o);
-      if (row < 0) continue;
-    }
-    const int e0 = __ldg(a.start + o), e1 = __ldg(a.start + o + 1);
-    uint4 acc = inf4;
-#pragma unroll 2
-    for (int e = e0; e < e1; e += 4) {
-      const uint2 ix = __ldg(reinterpret_cast<const uint2*>(a.lst + e));
-      const uint4 v0 = sm[(int)(ix.x & 0xFFFFu) * LR + lane];
-      const uint4 v1 = sm[(int)(ix.x >> 16) * LR + lane];
-      const uint4 v2 = sm[(int)(ix.y & 0xFFFFu) * LR + lane];
-      const uint4 v3 = sm[(int)(ix.y >> 16) * LR + lane];
-      acc.x = min3(min3(acc.x, v0.x, v1.x), v2.x, v3.x);
-      acc.y = min3(min3(acc.y, v0.y, v1.y), v2.y, v3.y);
-      acc.z = min3(min3(acc.z, v0.z, v1.z), v2.z, v3.z);
-      acc.w = min3(min3(acc.w, v0.w, v1.w), v2.w, v3.w);
-    }
-    if (!ok) continue;
-    if (FIRST) {
-      *reinterpret_cast<uint4*>(out + row * a.ldout + c) = acc;
-    } else {
-      const uint32_t w4[4] = {acc.x, acc.y, acc.z, acc.w};
-      if (c + 8 <= a.ncols) {
-        *reinterpret_cast<uint4*>(out + row * a.ldout + c) = acc;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 8; ++e)
-          if (c + e < a.ncols) out[row * a.ldout + c + e] = (int16_t)((w4[e >> 1] >> (16 * (e & 1))) & 0xFFFFu);
+      for (int u = 0; u < 4; ++u) {
+        v[u] = inf4;
+        if (ok && e[u] >= 0) {
+          if (FIRST) {
+            const uint4 x = __ldg(reinterpret_cast<const uint4*>(in + (int64_t)(e[u] >> 5) * a.ldin + c));
+            const uint32_t w2 = (uint32_t)(e[u] & 31) * 0x00010001u;
+            v[u] = make_uint4(__viaddmin_s16x2(x.x, w2, kInf2), __viaddmin_s16x2(x.y, w2, kInf2),
+                              __viaddmin_s16x2(x.z, w2, kInf2), __viaddmin_s16x2(x.w, w2, kInf2));
+          } else {
+            v[u] = __ldg(reinterpret_cast<const uint4*>(in + (int64_t)e[u] * a.ldin + c));
+          }
+        }
       }
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        if (c + e < a.ncols) {
-          const int32_t v = (int32_t)((w4[e >> 1] >> (16 * (e & 1))) & 0xFFFFu);
-          lmin = min(lmin, v);
-          if (c + e == row) ldiag = min(ldiag, v);
+      for (int u = 0; u < 4; ++u) {
+        const int s = s0 + u * G;
+        if (s < nst) sm[s * LR + lane] = v[u];
+      }
+    }
+    __syncthreads();
+
+    for (int g = gi; g < a.n_groups; g += G) {
+      uint4 acc[4] = {inf4, inf4, inf4, inf4};
+      // the group's record: the starts of its 7 sub-lists and their end
+      int b[kRec];
+      if (STAGED) {
+        const uint4 q = reinterpret_cast<const uint4*>(sgls)[g];
+        b[0] = q.x & 0xFFFF; b[1] = q.x >> 16; b[2] = q.y & 0xFFFF; b[3] = q.y >> 16;
+        b[4] = q.z & 0xFFFF; b[5] = q.z >> 16; b[6] = q.w & 0xFFFF; b[7] = q.w >> 16;
+      } else {
+        const int4* r4 = reinterpret_cast<const int4*>(a.gls + r0) + 2 * g;
+        const int4 q0 = __ldg(r4), q1 = __ldg(r4 + 1);
+        b[0] = q0.x - base; b[1] = q0.y - base; b[2] = q0.z - base; b[3] = q0.w - base;
+        b[4] = q1.x - base; b[5] = q1.y - base; b[6] = q1.z - base; b[7] = q1.w - base;
+      }
+      fold_sublist<0x1, LR>(acc, sm, pairs, b[0], b[1], lane);
+      fold_sublist<0x4, LR>(acc, sm, pairs, b[1], b[2], lane);
+      fold_sublist<0x5, LR>(acc, sm, pairs, b[2], b[3], lane);
+      fold_sublist<0x6, LR>(acc, sm, pairs, b[3], b[4], lane);
+      fold_sublist<0x7, LR>(acc, sm, pairs, b[4], b[5], lane);
+      fold_sublist<0xC, LR>(acc, sm, pairs, b[5], b[6], lane);
+      fold_sublist<0xD, LR>(acc, sm, pairs, b[6], b[7], lane);
+      if (!ok) continue;
+      const int4 rows = STAGED ? sgo[g] : __ldg(go4 + g);
+      const int32_t row4[4] = {rows.x, rows.y, rows.z, rows.w};
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const int64_t row = row4[l];
+        if (row < 0) continue;
+        if (FIRST) {
+          *reinterpret_cast<uint4*>(out + row * a.ldout + c) = acc[l];
+        } else {
+          const uint32_t w4[4] = {acc[l].x, acc[l].y, acc[l].z, acc[l].w};
+          if (c + 8 <= a.ncols) {
+            *reinterpret_cast<uint4*>(out + row * a.ldout + c) = acc[l];
+            m2 = min3(min3(m2, acc[l].x, acc[l].y), acc[l].z, acc[l].w);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              if (c + e < a.ncols) {
+                const int32_t v = (int32_t)((w4[e >> 1] >> (16 * (e & 1))) & 0xFFFFu);
+                out[row * a.ldout + c + e] = (int16_t)v;
+                lmin = min(lmin, v);
+              }
+            }
+          }
+          if ((uint64_t)(row - c) < 8) {
+            const int e = (int)(row - c);
+            ldiag = min(ldiag, (int32_t)((w4[e >> 1] >> (16 * (e & 1))) & 0xFFFFu));
+          }
         }
       }
     }
   }
 
   if (!FIRST && (a.min_out != nullptr || a.diag_out != nullptr)) {
+    lmin = min(lmin, (int32_t)min(m2 & 0xFFFFu, m2 >> 16));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       lmin = min(lmin, __shfl_xor_sync(0xFFFFFFFFu, lmin, o));
@@ -432,35 +714,90 @@ __global__ void __launch_bounds__(kSplitThreads) split_pass_kernel(SplitPass a) 
   }
 }
 
-size_t pass_smem(int n_slots, int W) { return (size_t)(n_slots + 1) * (size_t)W * 2; }
+constexpr size_t kSmemLimit = 220 * 1024;
 
-constexpr size_t kSmemTwoPerSm = 112 * 1024, kSmemMax = 220 * 1024;
+// Shared memory of a launch: rows and metadata when they fit (staged), else the rows alone.
+// Staging needs the fiber's list positions to fit the uint16 offsets.
+bool stageable(int max_list, size_t bytes, size_t limit) { return max_list <= 0xFFFF && bytes <= limit; }
 
-int choose_w(int n_slots) {
+size_t pass_smem(int max_slots, int n_groups, int max_list, int W, bool* staged) {
+  const size_t full = pass_smem_layout(max_slots, n_groups, max_list, W).bytes;
+  *staged = stageable(max_list, full, kSmemLimit);
+  return *staged ? full : (size_t)(max_slots + 1) * (size_t)W * 2;
+}
+
+// Slab width: 128 or 64 columns when the staged fiber leaves room for 3 CTAs per SM (narrower slabs
+// put more groups in a warp and cost shared-memory bank conflicts), else the widest that fits 2 or
+// 1; then the same for the rows alone.
+int choose_w(int max_slots, int n_groups, int max_list) {
   const int ws[3] = {128, 64, 32};
-  for (int w : ws)
-    if (pass_smem(n_slots, w) <= kSmemTwoPerSm) return w;
-  for (int w : ws)
-    if (pass_smem(n_slots, w) <= kSmemMax) return w;
+  const size_t limits[3] = {72 * 1024, 112 * 1024, kSmemLimit};
+  for (size_t lim : limits)
+    for (int w : ws)
+      if (stageable(max_list, pass_smem_layout(max_slots, n_groups, max_list, w).bytes, lim)) return w;
+  for (size_t lim : limits)
+    for (int w : ws)
+      if ((size_t)(max_slots + 1) * (size_t)w * 2 <= lim) return w;
   return 0;
 }
 
-bool valid_w(int W, int n_slots) {
-  return (W == 32 || W == 64 || W == 128) && pass_smem(n_slots, W) <= kSmemMax;
+bool valid_w(int W, int max_slots) {
+  return (W == 32 || W == 64 || W == 128) && (size_t)(max_slots + 1) * (size_t)W * 2 <= kSmemLimit;
+}
+
+// The pass kernels' dynamic shared-memory limit, raised once per device to kSmemLimit (the limit is
+// a ceiling: occupancy follows each launch's own request).  rd_split_plan does it, so that no
+// attribute call falls inside a stream capture of the steps.
+template <bool FIRST, bool RING>
+cudaError_t raise_limits() {
+  void (*ks[6])(SplitPass) = {split_pass_kernel<128, FIRST, RING, true>,  split_pass_kernel<64, FIRST, RING, true>,
+                              split_pass_kernel<32, FIRST, RING, true>,   split_pass_kernel<128, FIRST, RING, false>,
+                              split_pass_kernel<64, FIRST, RING, false>,  split_pass_kernel<32, FIRST, RING, false>};
+  for (auto k : ks) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+std::mutex g_limits_mu;
+uint64_t g_limits_done = 0;  // one bit per device
+
+cudaError_t ensure_limits() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_limits_mu);
+  if (dev < 64 && ((g_limits_done >> dev) & 1u)) return cudaSuccess;
+  e = raise_limits<true, false>();
+  if (e == cudaSuccess) e = raise_limits<false, false>();
+  if (e == cudaSuccess) e = raise_limits<true, true>();
+  if (e == cudaSuccess) e = raise_limits<false, true>();
+  if (e == cudaSuccess && dev < 64) g_limits_done |= 1ull << dev;
+  return e;
 }
 
 template <bool FIRST, bool RING>
 cudaError_t launch_pass(const SplitPass& a, int W, int64_t fibers, cudaStream_t s) {
-  const size_t smem = pass_smem(a.n_slots, W);
+  bool staged = false;
+  const size_t smem = pass_smem(a.max_slots, a.n_groups, a.max_list, W, &staged);
   const int64_t slabs = (a.ncols + W - 1) / W;
-  const dim3 grid((unsigned)slabs, (unsigned)fibers);
+  const dim3 grid((unsigned)((slabs + a.slabs_per_cta - 1) / a.slabs_per_cta), (unsigned)fibers);
   void (*k)(SplitPass) = nullptr;
-  switch (W) {
-    case 128: k = split_pass_kernel<128, FIRST, RING>; break;
-    case 64: k = split_pass_kernel<64, FIRST, RING>; break;
-    default: k = split_pass_kernel<32, FIRST, RING>; break;
+  if (staged) {
+    switch (W) {
+      case 128: k = split_pass_kernel<128, FIRST, RING, true>; break;
+      case 64: k = split_pass_kernel<64, FIRST, RING, true>; break;
+      default: k = split_pass_kernel<32, FIRST, RING, true>; break;
+    }
+  } else {
+    switch (W) {
+      case 128: k = split_pass_kernel<128, FIRST, RING, false>; break;
+      case 64: k = split_pass_kernel<64, FIRST, RING, false>; break;
+      default: k = split_pass_kernel<32, FIRST, RING, false>; break;
+    }
   }
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_limits();
   if (e != cudaSuccess) return e;
   k<<<grid, kSplitThreads, smem, s>>>(a);
   return cudaGetLastError();
@@ -473,17 +810,23 @@ void passes_of(const rd_split_info_t& info, const void* plan, SplitPass* p1, Spl
   *p1 = SplitPass{};
   *p2 = SplitPass{};
   p1->ncols = p2->ncols = info.N;
-  p1->n_slots = info.n_rho;
-  p1->n_out = info.n_pi;
-  p1->n_sigma = p2->n_sigma = info.n_sigma;
-  p1->src = at<int32_t>(plan, L.fiber);
-  p1->start = at<int32_t>(plan, L.c1s);
-  p1->lst = at<uint16_t>(plan, L.c1);
-  p2->n_slots = info.n_sigma;
-  p2->n_out = info.n_phi;
-  p2->start = at<int32_t>(plan, L.c2s);
-  p2->lst = at<uint16_t>(plan, L.c2);
-  p2->dst = at<int32_t>(plan, L.outrow);
+  p1->n_groups = (int32_t)L.nG1;
+  p1->max_slots = info.slots1;
+  p1->max_list = info.lmax1;
+  p1->slabs_per_cta = info.k1;
+  p1->fstart = at<int32_t>(plan, L.fstart1);
+  p1->fmem = at<int32_t>(plan, L.fmem1);
+  p1->gls = at<int32_t>(plan, L.gls1);
+  p1->lst = at<uint16_t>(plan, L.l1);
+  p1->go = at<int32_t>(plan, L.go1);
+  p2->n_groups = (int32_t)L.nG2;
+  p2->max_slots = info.slots2;
+  p2->max_list = info.lmax2;
+  p2->slabs_per_cta = info.k2;
+  p2->fstart = at<int32_t>(plan, L.fstart2);
+  p2->gls = at<int32_t>(plan, L.gls2);
+  p2->lst = at<uint16_t>(plan, L.l2);
+  p2->go = at<int32_t>(plan, L.go2);
 }
 
 bool info_ok(const rd_split_info_t* info, const void* plan) {
@@ -492,7 +835,11 @@ bool info_ok(const rd_split_info_t* info, const void* plan) {
   if (!make_layout(info->m, info->j, &L)) return false;
   if (info->N != L.N || info->n_pi != L.nPi || info->n_phi != L.nPhi) return false;
   if (info->n_rho < 1 || info->n_rho > L.rhoB || info->n_sigma < 1 || info->n_sigma > L.sigB) return false;
-  return valid_w(info->w1, info->n_rho) && valid_w(info->w2, info->n_sigma);
+  if (info->slots1 < 1 || info->slots1 > L.nPi || info->slots2 < 1 || info->slots2 > info->n_sigma) return false;
+  if (info->x_rows < 1 || info->x_rows > (int64_t)L.nPi * info->n_sigma) return false;
+  if (info->lmax1 < 0 || info->lmax2 < 0 || info->k1 < 1 || info->k1 > 64 || info->k2 < 1 || info->k2 > 64)
+    return false;
+  return valid_w(info->w1, info->slots1) && valid_w(info->w2, info->slots2);
 }
 
 struct SplitCtx {
@@ -522,9 +869,53 @@ rd_status fail(cudaError_t e) {
   return RD_ERR_CUDA;
 }
 
+}  // namespace
+
+bool split_ring_ok(const SplitRing& d, int64_t N) {
+  return info_ok(&d.info, d.plan) && d.info.N == N && d.X != nullptr && aligned16(d.X) && d.ldx >= N &&
+         d.ldx % 8 == 0;
+}
+
+cudaError_t split_ring_product(const SplitRing& d, PowerState* st, int16_t* ring, int64_t slot_elems, int slots,
+                               int64_t ld, cudaStream_t s) {
+  SplitCtx c{};
+  passes_of(d.info, d.plan, &c.p1, &c.p2);
+  c.p1.out = d.X;
+  c.p1.ldout = d.ldx;
+  c.p2.in = d.X;
+  c.p2.ldin = d.ldx;
+  c.w1 = d.info.w1;
+  c.w2 = d.info.w2;
+  c.fibers1 = d.info.n_sigma;
+  c.fibers2 = d.info.n_pi;
+  Run r{};
+  r.st = st;
+  r.ring = ring;
+  r.slot_elems = slot_elems;
+  r.slots = slots;
+  r.N = d.info.N;
+  r.ld = ld;
+  return split_power_product(r, &c, s);
+}
+
+namespace {
+
 unsigned grid_for(int64_t n) {
   const int64_t g = (n + 255) / 256;
   return (unsigned)(g < 1 ? 1 : (g > 65535 ? 65535 : g));
+}
+
+// Flags and exclusive ranks of the correct words of len letters (len may be 0), total in rank[4^len].
+void rank_correct(int32_t* rank, int len, cudaStream_t s) {
+  const int64_t n = ipow(4, len);
+  correct_flag_kernel<<<grid_for(n), 256, 0, s>>>(rank, len, n);
+  scan_i32_kernel<<<1, 1024, 0, s>>>(rank, n);
+}
+
+cudaError_t read_i32(const int32_t* dev, int32_t* host, int n, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(host, dev, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
 }
 
 }  // namespace
@@ -554,51 +945,45 @@ extern "C" rd_status rd_split_plan(int m, int j, void* plan_dev, size_t plan_byt
   if (L.N * 32 > 0x7FFFFFFFll) return RD_ERR_ARG;
   void* P = plan_dev;
   const int h = L.h;
-  const int64_t n5j = ipow(kTauCount, j), n5h = ipow(kTauCount, h), n4j = ipow(4, j), n4h = ipow(4, h);
-  cudaError_t e = cudaSuccess;
+  const int64_t n5j = ipow(kTauCount, j), n5h = ipow(kTauCount, h);
+  int32_t* counters = at<int32_t>(P, L.counters);
+  cudaError_t e0 = ensure_limits();
+  if (e0 != cudaSuccess) return fail(e0);
   rd_status rc = rd_enumerate_states(m, at<uint32_t>(P, L.codes), at<uint8_t>(P, L.wts), s);
   if (rc != RD_OK) return rc;
-  e = cudaMemsetAsync(at<int32_t>(P, L.rankR), 0, (size_t)(n5j + 1) * 4, s);
+  cudaError_t e = cudaMemsetAsync(at<int32_t>(P, L.rankR), 0, (size_t)(n5j + 1) * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(at<int32_t>(P, L.rankS), 0, (size_t)(n5h + 1) * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 8 * 4, s);
   if (e != cudaSuccess) return fail(e);
   split_mark_kernel<<<grid_for(L.N), 256, 0, s>>>(at<uint32_t>(P, L.codes), L.N, m, j, at<int32_t>(P, L.rankR),
                                                    at<int32_t>(P, L.rankS));
-  correct_flag_kernel<<<grid_for(n4j), 256, 0, s>>>(at<int32_t>(P, L.rankPi), j, n4j);
-  correct_flag_kernel<<<grid_for(n4h), 256, 0, s>>>(at<int32_t>(P, L.rankPhi), h, n4h);
   scan_i32_kernel<<<1, 1024, 0, s>>>(at<int32_t>(P, L.rankR), n5j);
   scan_i32_kernel<<<1, 1024, 0, s>>>(at<int32_t>(P, L.rankS), n5h);
-  scan_i32_kernel<<<1, 1024, 0, s>>>(at<int32_t>(P, L.rankPi), n4j);
-  scan_i32_kernel<<<1, 1024, 0, s>>>(at<int32_t>(P, L.rankPhi), n4h);
+  // the correct words of j, h, j - 1 and h - 1 letters; the last two are the output groups
+  rank_correct(at<int32_t>(P, L.rankPi), j, s);
+  rank_correct(at<int32_t>(P, L.rankPhi), h, s);
+  rank_correct(at<int32_t>(P, L.rankG1), j - 1, s);
+  rank_correct(at<int32_t>(P, L.rankG2), h - 1, s);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(e);
-  int32_t cnt[4] = {0, 0, 0, 0};
-  e = cudaMemcpyAsync(&cnt[0], at<int32_t>(P, L.rankR) + n5j, 4, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt[1], at<int32_t>(P, L.rankS) + n5h, 4, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt[2], at<int32_t>(P, L.rankPi) + n4j, 4, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt[3], at<int32_t>(P, L.rankPhi) + n4h, 4, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int32_t cnt[6] = {0, 0, 0, 0, 0, 0};
+  const int32_t* totals[6] = {at<int32_t>(P, L.rankR) + n5j,         at<int32_t>(P, L.rankS) + n5h,
+                              at<int32_t>(P, L.rankPi) + ipow(4, j), at<int32_t>(P, L.rankPhi) + ipow(4, h),
+                              at<int32_t>(P, L.rankG1) + ipow(4, j - 1), at<int32_t>(P, L.rankG2) + ipow(4, h - 1)};
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = read_i32(totals[i], &cnt[i], 1, s);
   if (e != cudaSuccess) return fail(e);
   const int64_t n_rho = cnt[0], n_sigma = cnt[1];
-  // the bounds are exact upper bounds and the prefix / suffix words are the correct words
+  // the type counts are within their bounds, and the letter words counted are the correct words
   if (n_rho < 1 || n_rho > L.rhoB || n_sigma < 1 || n_sigma > L.sigB || cnt[2] != L.nPi || cnt[3] != L.nPhi ||
-      n_rho > 0xFFFF || n_sigma > 0xFFFF)
+      cnt[4] != L.nG1 || cnt[5] != L.nG2 || L.nPi >= 0xFFFF || n_sigma >= 0xFFFF)
     return RD_ERR_RANGE;
-  const int w1 = choose_w((int)n_rho), w2 = choose_w((int)n_sigma);
-  if (w1 == 0 || w2 == 0) return RD_ERR_ARG;  // a fiber does not fit in shared memory
   invert_kernel<<<grid_for(n5j), 256, 0, s>>>(at<int32_t>(P, L.rankR), n5j, at<int32_t>(P, L.rhoCode));
   invert_kernel<<<grid_for(n5h), 256, 0, s>>>(at<int32_t>(P, L.rankS), n5h, at<int32_t>(P, L.sigCode));
-  invert_kernel<<<grid_for(n4j), 256, 0, s>>>(at<int32_t>(P, L.rankPi), n4j, at<int32_t>(P, L.piCode));
-  invert_kernel<<<grid_for(n4h), 256, 0, s>>>(at<int32_t>(P, L.rankPhi), n4h, at<int32_t>(P, L.phiCode));
-  list_count_kernel<<<grid_for(L.nPi), 256, 0, s>>>(at<int32_t>(P, L.piCode), L.nPi, at<int32_t>(P, L.rhoCode),
-                                                    n_rho, j, at<int32_t>(P, L.c1s));
-  list_count_kernel<<<grid_for(L.nPhi), 256, 0, s>>>(at<int32_t>(P, L.phiCode), L.nPhi, at<int32_t>(P, L.sigCode),
-                                                     n_sigma, h, at<int32_t>(P, L.c2s));
-  scan_i32_kernel<<<1, 1024, 0, s>>>(at<int32_t>(P, L.c1s), L.nPi);
-  scan_i32_kernel<<<1, 1024, 0, s>>>(at<int32_t>(P, L.c2s), L.nPhi);
-  list_fill_kernel<<<grid_for(L.nPi), 256, 0, s>>>(at<int32_t>(P, L.piCode), L.nPi, at<int32_t>(P, L.rhoCode), n_rho,
-                                                   j, at<int32_t>(P, L.c1s), at<uint16_t>(P, L.c1));
-  list_fill_kernel<<<grid_for(L.nPhi), 256, 0, s>>>(at<int32_t>(P, L.phiCode), L.nPhi, at<int32_t>(P, L.sigCode),
-                                                    n_sigma, h, at<int32_t>(P, L.c2s), at<uint16_t>(P, L.c2));
+  invert_kernel<<<grid_for(ipow(4, j)), 256, 0, s>>>(at<int32_t>(P, L.rankPi), ipow(4, j), at<int32_t>(P, L.piCode));
+  invert_kernel<<<grid_for(ipow(4, j - 1)), 256, 0, s>>>(at<int32_t>(P, L.rankG1), ipow(4, j - 1),
+                                                         at<int32_t>(P, L.g1Code));
+  invert_kernel<<<grid_for(ipow(4, h - 1)), 256, 0, s>>>(at<int32_t>(P, L.rankG2), ipow(4, h - 1),
+                                                         at<int32_t>(P, L.g2Code));
   e = cudaMemsetAsync(at<int32_t>(P, L.fiber), 0xFF, (size_t)n_sigma * (size_t)n_rho * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(at<int32_t>(P, L.outrow), 0xFF, (size_t)L.nPi * (size_t)L.nPhi * 4, s);
   if (e != cudaSuccess) return fail(e);
@@ -606,10 +991,77 @@ extern "C" rd_status rd_split_plan(int m, int j, void* plan_dev, size_t plan_byt
                                                    at<int32_t>(P, L.rankS), n_rho, at<int32_t>(P, L.rankPi),
                                                    at<int32_t>(P, L.rankPhi), L.nPhi, at<int32_t>(P, L.fiber),
                                                    at<int32_t>(P, L.outrow));
+  // pass-1 fibers in compact form, then the finite rows of X and the pass-2 fibers
+  fiber_count_kernel<<<grid_for(n_sigma), 256, 0, s>>>(at<int32_t>(P, L.fiber), n_sigma, n_rho,
+                                                       at<int32_t>(P, L.fstart1));
+  scan_i32_kernel<<<1, 1024, 0, s>>>(at<int32_t>(P, L.fstart1), n_sigma);
+  fiber_fill_kernel<<<grid_for(n_sigma), 256, 0, s>>>(at<int32_t>(P, L.fiber), n_sigma, n_rho,
+                                                      at<int32_t>(P, L.fstart1), at<int32_t>(P, L.fmem1),
+                                                      at<int32_t>(P, L.frho1), counters + 0);
+  const int64_t nx = L.nPi * n_sigma;
+  xflag_kernel<<<grid_for(nx), 256, 0, s>>>(at<int32_t>(P, L.piCode), L.nPi, n_sigma, at<int32_t>(P, L.fstart1),
+                                             at<int32_t>(P, L.frho1), at<int32_t>(P, L.rhoCode), j,
+                                             at<int32_t>(P, L.xrank));
+  scan_i32_kernel<<<1, 1024, 0, s>>>(at<int32_t>(P, L.xrank), nx);
+  xsig_kernel<<<grid_for(nx), 256, 0, s>>>(at<int32_t>(P, L.xrank), L.nPi, n_sigma, at<int32_t>(P, L.xsig),
+                                            at<int32_t>(P, L.fstart2), counters + 1);
   e = cudaGetLastError();
-  int32_t tot[2] = {0, 0};
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&tot[0], at<int32_t>(P, L.c1s) + L.nPi, 4, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&tot[1], at<int32_t>(P, L.c2s) + L.nPhi, 4, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return fail(e);
+  int32_t c2[2] = {0, 0}, x_rows = 0;
+  e = read_i32(counters, c2, 2, s);
+  if (e == cudaSuccess) e = read_i32(at<int32_t>(P, L.xrank) + nx, &x_rows, 1, s);
+  if (e != cudaSuccess) return fail(e);
+  const int32_t slots1 = c2[0], slots2 = c2[1];
+  if (slots1 < 1 || slots1 > L.nPi || slots2 < 1 || slots2 > n_sigma || x_rows < 1) return RD_ERR_RANGE;
+
+  GroupArgs g1{};
+  g1.first = 1;
+  g1.len = j;
+  g1.n_fibers = n_sigma;
+  g1.n_groups = L.nG1;
+  g1.gcode = at<int32_t>(P, L.g1Code);
+  g1.fstart = at<int32_t>(P, L.fstart1);
+  g1.slot_tc = at<int32_t>(P, L.frho1);
+  g1.tcode = at<int32_t>(P, L.rhoCode);
+  GroupArgs g2{};
+  g2.first = 0;
+  g2.len = h;
+  g2.n_fibers = L.nPi;
+  g2.n_groups = L.nG2;
+  g2.gcode = at<int32_t>(P, L.g2Code);
+  g2.fstart = at<int32_t>(P, L.fstart2);
+  g2.slot_tc = at<int32_t>(P, L.xsig);
+  g2.tcode = at<int32_t>(P, L.sigCode);
+  g2.piCode = at<int32_t>(P, L.piCode);
+  const int64_t nrec1 = n_sigma * L.nG1, nrec2 = L.nPi * L.nG2;
+  group_lists_kernel<false><<<grid_for(nrec1), 256, 0, s>>>(g1, at<int32_t>(P, L.gls1), nullptr, counters + 4);
+  group_lists_kernel<false><<<grid_for(nrec2), 256, 0, s>>>(g2, at<int32_t>(P, L.gls2), nullptr, counters + 4);
+  scan_i32_kernel<<<1, 1024, 0, s>>>(at<int32_t>(P, L.gls1), nrec1 * kRec);
+  scan_i32_kernel<<<1, 1024, 0, s>>>(at<int32_t>(P, L.gls2), nrec2 * kRec);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(e);
+  int32_t tot[3] = {0, 0, 0};
+  e = read_i32(at<int32_t>(P, L.gls1) + nrec1 * kRec, &tot[0], 1, s);
+  if (e == cudaSuccess) e = read_i32(at<int32_t>(P, L.gls2) + nrec2 * kRec, &tot[1], 1, s);
+  if (e == cudaSuccess) e = read_i32(counters + 4, &tot[2], 1, s);
+  if (e != cudaSuccess) return fail(e);
+  // a target set outside the 7 would be a slip in the rules above: refuse the plan
+  if (tot[0] > L.l1B || tot[1] > L.l2B || tot[2] != 0) return RD_ERR_RANGE;
+  fiber_list_max_kernel<<<grid_for(n_sigma), 256, 0, s>>>(at<int32_t>(P, L.gls1), n_sigma, L.nG1, counters + 2);
+  fiber_list_max_kernel<<<grid_for(L.nPi), 256, 0, s>>>(at<int32_t>(P, L.gls2), L.nPi, L.nG2, counters + 3);
+  int32_t lm[2] = {0, 0};
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = read_i32(counters + 2, lm, 2, s);
+  if (e != cudaSuccess) return fail(e);
+  const int w1 = choose_w(slots1, (int)L.nG1, lm[0]), w2 = choose_w(slots2, (int)L.nG2, lm[1]);
+  if (w1 == 0 || w2 == 0) return RD_ERR_ARG;  // a fiber does not fit in shared memory
+  group_lists_kernel<true><<<grid_for(nrec1), 256, 0, s>>>(g1, at<int32_t>(P, L.gls1), at<uint16_t>(P, L.l1), nullptr);
+  group_lists_kernel<true><<<grid_for(nrec2), 256, 0, s>>>(g2, at<int32_t>(P, L.gls2), at<uint16_t>(P, L.l2), nullptr);
+  group_out_kernel<<<grid_for(nrec1), 256, 0, s>>>(g1, at<int32_t>(P, L.rankPi), at<int32_t>(P, L.xrank), n_sigma,
+                                                   nullptr, 0, at<int32_t>(P, L.go1));
+  group_out_kernel<<<grid_for(nrec2), 256, 0, s>>>(g2, at<int32_t>(P, L.rankPhi), nullptr, 0,
+                                                   at<int32_t>(P, L.outrow), L.nPhi, at<int32_t>(P, L.go2));
+  e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(e);
   *info = rd_split_info_t{};
@@ -622,10 +1074,16 @@ extern "C" rd_status rd_split_plan(int m, int j, void* plan_dev, size_t plan_byt
   info->n_phi = (int32_t)L.nPhi;
   info->list1_entries = tot[0];
   info->list2_entries = tot[1];
-  info->x_rows = L.nPi * n_sigma;
+  info->x_rows = x_rows;
   info->plan_bytes = L.bytes;
   info->w1 = w1;
   info->w2 = w2;
+  info->slots1 = slots1;
+  info->slots2 = slots2;
+  info->lmax1 = lm[0];
+  info->lmax2 = lm[1];
+  info->k1 = kDefaultSlabsPerCta;
+  info->k2 = kDefaultSlabsPerCta;
   return RD_OK;
 }
 

@@ -83,7 +83,8 @@ def test_split_minplus_matches_oracle(rd, torch_mod, orc, m, j):
     assert (info.m, info.j, info.N) == (m, j, n)
     assert (info.n_rho, info.n_sigma) == type_counts(orc, m, j)
     assert (info.n_pi, info.n_phi) == (rd.state_count(j), rd.state_count(m - j))
-    assert info.x_rows == info.n_pi * info.n_sigma
+    assert 0 < info.x_rows <= info.n_pi * info.n_sigma
+    assert 0 < info.slots1 <= info.n_pi and 0 < info.slots2 <= info.n_sigma
     C = torch.full((n, B.stride(0)), 777, dtype=torch.int16, device="cuda")
     mn = torch.zeros(1, dtype=torch.int32, device="cuda")
     rd.split_minplus(plan, B, C, min_out=mn)
@@ -281,3 +282,29 @@ def test_power_split_m10(rd, torch_mod, orc):
         assert np.all(d == d[0]), k
     del work, plan, A
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("graph_steps", [0, 8])
+def test_power_multi_mixes_split_and_sparse_runs(rd, torch_mod, orc, graph_steps):
+    """rd_power_until_periodic_multi with row-split runs (even m) beside sparse runs (odd m), with and
+    without the CUDA graph: each run's relation and gamma sequence equal the oracle's (m <= 7) and
+    Table 2 (m = 8, 9)."""
+    kmax = 48
+    runs = []
+    for m in range(1, 10):
+        A, n = rd.transfer_matrix(m)
+        plan = rd.split_plan(m, x_ld=A.stride(0)) if m % 2 == 0 else rd.sparse_plan(A, n, n, 2)
+        runs.append((A, n, plan, rd.power_workspace(n, A.stride(0), kmax, 8)))
+    res = rd.power_until_periodic_multi(runs, 2, kmax, graph_steps=graph_steps)
+    table = {int(x[0]): tuple(map(int, x[1:])) for x in read_golden("paper_table2_periods.txt")}
+    for m, r in zip(range(1, 10), res):
+        assert r["found"], m
+        if m <= 7:
+            o = orc.power_until_periodic(m, kmax=kmax)
+            assert (r["k"], r["p"], r["q"]) == (o["k"], o["p"], o["q"]), m
+            assert np.array_equal(r["gamma"][1:r["j"] + 1], o["gamma"][1:o["j"] + 1]), m
+        if m in table:  # the first repeat implies the printed relation (at m = 4 its period 1 divides 5)
+            n0, alpha, beta = table[m]
+            assert n0 >= r["k"] and alpha % r["p"] == 0 and beta == r["q"] * (alpha // r["p"]), m
+    for nn in range(3, 8):
+        assert res[8]["gamma"][nn] == orc.row_dp(9, nn)
