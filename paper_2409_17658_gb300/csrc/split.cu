@@ -169,7 +169,8 @@ struct Layout {
   int m, j, h;
   int64_t N, nPi, nPhi, nG1, nG2, rhoB, sigB, l1B, l2B;
   size_t codes, wts, rankR, rankS, rankPi, rankPhi, rankG1, rankG2, rhoCode, sigCode, piCode, g1Code, g2Code, fiber,
-      outrow, fstart1, fmem1, frho1, xrank, xsig, fstart2, gls1, l1, go1, gls2, l2, go2, counters, bytes;
+      outrow, fstart1, fmem1, frho1, xrank, xsig, fstart2, gls1, l1, go1, ord1, gls2, l2, go2, ord2, counters,
+      bytes;
 };
 
 bool make_layout(int m, int j, Layout* L) {
@@ -220,9 +221,11 @@ bool make_layout(int m, int j, Layout* L) {
   L->gls1 = take(((size_t)L->sigB * (size_t)L->nG1 * kRec + 1) * 4);
   L->l1 = take((size_t)L->l1B * 2);
   L->go1 = take((size_t)L->sigB * (size_t)L->nG1 * 4 * 4);
+  L->ord1 = take((size_t)L->sigB * (size_t)L->nG1 * 2);
   L->gls2 = take(((size_t)L->nPi * (size_t)L->nG2 * kRec + 1) * 4);
   L->l2 = take((size_t)L->l2B * 2);
   L->go2 = take((size_t)L->nPi * (size_t)L->nG2 * 4 * 4);
+  L->ord2 = take((size_t)L->nPi * (size_t)L->nG2 * 2);
   L->counters = take(8 * 4);
   L->bytes = off;
   return true;
@@ -435,6 +438,26 @@ __global__ void group_lists_kernel(GroupArgs a, int32_t* cnt_or_start, uint16_t*
   }
 }
 
+// Each fiber's groups in decreasing list length (ties by index): the kernel deals them to its lane
+// sets in that order, back and forth, so the sets get similar work.
+__global__ void group_order_kernel(const int32_t* gls, int64_t n_fibers, int64_t n_groups, uint16_t* ord) {
+  GRID_STRIDE(f, n_fibers) {
+    uint16_t* o = ord + f * n_groups;
+    const int32_t* r = gls + f * n_groups * kRec;
+    for (int64_t g = 0; g < n_groups; ++g) {
+      const int32_t len = r[g * kRec + kRec - 1] - r[g * kRec];
+      int64_t i = g;
+      while (i > 0) {
+        const int64_t h = o[i - 1];
+        if (r[h * kRec + kRec - 1] - r[h * kRec] >= len) break;
+        o[i] = o[i - 1];
+        --i;
+      }
+      o[i] = (uint16_t)g;
+    }
+  }
+}
+
 // The list entries of each fiber (its records are contiguous), maximum into *out.
 __global__ void fiber_list_max_kernel(const int32_t* gls, int64_t n_fibers, int64_t n_groups, int32_t* out) {
   GRID_STRIDE(f, n_fibers) {
@@ -484,6 +507,7 @@ struct SplitPass {
   const int32_t* gls;     // [8 (fibers G) + 1] per (fiber, group): the 7 sub-list starts (even), then the end
   const uint16_t* lst;    // 1-based slot numbers, 0 = dummy
   const int32_t* go;      // [(fibers G) * 4] output rows per boundary letter, or -1
+  const uint16_t* ord;    // [fibers G] each fiber's groups in decreasing list length
   int32_t* min_out;
   int32_t* diag_out;
   PowerState* st;  // ring mode: B = power slot k (pass 1), R = slot k + 1 (pass 2)
@@ -529,10 +553,10 @@ __device__ __forceinline__ void fold_sublist(uint4 (&acc)[4], const uint4* sm, c
 }
 
 // Shared memory of one CTA: the staged rows, then the fiber's sub-list bounds (uint16, local to the
-// fiber's list), its output rows (int32), its list (uint16) and its words (pass 1, int32), each part
-// 16-byte aligned.
+// fiber's list), its output rows (int32), its list (uint16), its words (pass 1, int32) and its group
+// order (uint16), each part 16-byte aligned.
 struct PassSmem {
-  size_t gls, go, lst, mem, bytes;
+  size_t gls, go, lst, mem, ord, bytes;
 };
 __host__ __device__ inline PassSmem pass_smem_layout(int max_slots, int n_groups, int max_list, int W) {
   PassSmem p;
@@ -541,7 +565,8 @@ __host__ __device__ inline PassSmem pass_smem_layout(int max_slots, int n_groups
   p.go = p.gls + (size_t)n_groups * kRec * 2;
   p.lst = p.go + (size_t)n_groups * 4 * 4;
   p.mem = p.lst + ((size_t)max_list * 2 + 15) / 16 * 16;
-  p.bytes = p.mem + ((size_t)max_slots * 4 + 15) / 16 * 16;
+  p.ord = p.mem + ((size_t)max_slots * 4 + 15) / 16 * 16;
+  p.bytes = p.ord + ((size_t)n_groups * 2 + 15) / 16 * 16;
   return p;
 }
 
@@ -573,6 +598,8 @@ __global__ void __launch_bounds__(kSplitThreads) split_pass_kernel(SplitPass a) 
   int4* sgo = reinterpret_cast<int4*>(smb + lay.go);
   uint32_t* slst = reinterpret_cast<uint32_t*>(smb + lay.lst);
   int32_t* smem_words = reinterpret_cast<int32_t*>(smb + lay.mem);
+  uint16_t* sord = reinterpret_cast<uint16_t*>(smb + lay.ord);
+  const uint16_t* gord = a.ord + f * a.n_groups;
   const int64_t r0 = f * a.n_groups * kRec;
   const int32_t base = __ldg(a.gls + r0);
   const int4* go4 = reinterpret_cast<const int4*>(a.go) + f * a.n_groups;
@@ -587,6 +614,7 @@ __global__ void __launch_bounds__(kSplitThreads) split_pass_kernel(SplitPass a) 
     for (int i = threadIdx.x; i < npairs; i += kSplitThreads) slst[i] = __ldg(glst + i);
     if (FIRST)
       for (int i = threadIdx.x; i < nst - 1; i += kSplitThreads) smem_words[i] = __ldg(a.fmem + f0 + i);
+    for (int i = threadIdx.x; i < a.n_groups; i += kSplitThreads) sord[i] = gord[i];
   }
   const uint32_t* pairs = STAGED ? slst : glst;
   int32_t lmin = kInf, ldiag = kInf;
@@ -634,7 +662,11 @@ __global__ void __launch_bounds__(kSplitThreads) split_pass_kernel(SplitPass a) 
     }
     __syncthreads();
 
-    for (int g = gi; g < a.n_groups; g += G) {
+    // groups in decreasing work, dealt to the lane sets back and forth (0..G-1, G-1..0, ...)
+    for (int round0 = 0; round0 < a.n_groups; round0 += G) {
+      const int idx = round0 + (((round0 / G) & 1) ? (G - 1 - gi) : gi);
+      if (idx >= a.n_groups) continue;
+      const int g = STAGED ? sord[idx] : __ldg(gord + idx);
       uint4 acc[4] = {inf4, inf4, inf4, inf4};
       // the group's record: the starts of its 7 sub-lists and their end
       int b[kRec];
@@ -819,6 +851,7 @@ void passes_of(const rd_split_info_t& info, const void* plan, SplitPass* p1, Spl
   p1->gls = at<int32_t>(plan, L.gls1);
   p1->lst = at<uint16_t>(plan, L.l1);
   p1->go = at<int32_t>(plan, L.go1);
+  p1->ord = at<uint16_t>(plan, L.ord1);
   p2->n_groups = (int32_t)L.nG2;
   p2->max_slots = info.slots2;
   p2->max_list = info.lmax2;
@@ -827,6 +860,7 @@ void passes_of(const rd_split_info_t& info, const void* plan, SplitPass* p1, Spl
   p2->gls = at<int32_t>(plan, L.gls2);
   p2->lst = at<uint16_t>(plan, L.l2);
   p2->go = at<int32_t>(plan, L.go2);
+  p2->ord = at<uint16_t>(plan, L.ord2);
 }
 
 bool info_ok(const rd_split_info_t* info, const void* plan) {
@@ -1057,6 +1091,8 @@ extern "C" rd_status rd_split_plan(int m, int j, void* plan_dev, size_t plan_byt
   if (w1 == 0 || w2 == 0) return RD_ERR_ARG;  // a fiber does not fit in shared memory
   group_lists_kernel<true><<<grid_for(nrec1), 256, 0, s>>>(g1, at<int32_t>(P, L.gls1), at<uint16_t>(P, L.l1), nullptr);
   group_lists_kernel<true><<<grid_for(nrec2), 256, 0, s>>>(g2, at<int32_t>(P, L.gls2), at<uint16_t>(P, L.l2), nullptr);
+  group_order_kernel<<<grid_for(n_sigma), 64, 0, s>>>(at<int32_t>(P, L.gls1), n_sigma, L.nG1, at<uint16_t>(P, L.ord1));
+  group_order_kernel<<<grid_for(L.nPi), 64, 0, s>>>(at<int32_t>(P, L.gls2), L.nPi, L.nG2, at<uint16_t>(P, L.ord2));
   group_out_kernel<<<grid_for(nrec1), 256, 0, s>>>(g1, at<int32_t>(P, L.rankPi), at<int32_t>(P, L.xrank), n_sigma,
                                                    nullptr, 0, at<int32_t>(P, L.go1));
   group_out_kernel<<<grid_for(nrec2), 256, 0, s>>>(g2, at<int32_t>(P, L.rankPhi), nullptr, 0,
