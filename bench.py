@@ -269,6 +269,30 @@ def run_sparse_only(rd, torch, args) -> None:
                       "b_row_TBps": plan["entries"] * n * 2 / (ms * 1e-3) / 1e12}))
 
 
+def run_split_only(rd, torch, args) -> None:
+    """One row-split product A(G) (x) P with P = A(G)^2, repeated: the kernel pair of the power step."""
+    m = args.split_only
+    A, n = rd.transfer_matrix(m)
+    P = torch.empty_like(A)
+    C = torch.empty_like(A)
+    plan = rd.split_plan(m, x_ld=A.stride(0))
+    rd.split_minplus(plan, A, P)  # P = A (x) A, dense enough to stand for a power
+    for _ in range(args.warmup):
+        rd.split_minplus(plan, P, C)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for s0, s1 in evs:
+        s0.record()
+        rd.split_minplus(plan, P, C)
+        s1.record()
+    torch.cuda.synchronize()
+    ms = float(np.mean([s0.elapsed_time(s1) for s0, s1 in evs]))
+    info = plan["info"]
+    moved = (2 * n + 2 * info.x_rows) * n * 2
+    print(json.dumps({"split_only_m": m, "N": n, "plan": info.as_dict(), "ms": ms, "bytes_per_product": moved,
+                      "GBps": moved / (ms * 1e-3) / 1e9, "frac_of_measured_hbm": moved / (ms * 1e-3) / 1e9 / HBM_GBS}))
+
+
 def gemv_leg(rd, torch, B, n: int, reps: int = 20) -> dict:
     """The matrix-vector form of the synthetic workload: y = x (x) B at N = 16384, against HBM bandwidth."""
     from paper_2409_17658_gb300 import inputs
@@ -463,6 +487,8 @@ def main() -> None:
     ap.add_argument("--sparse-only", type=int, default=0, metavar="M",
                     help="time only the dense x sparse product A(G) (x) A(G)^2 for m = M (profiler captures)")
     ap.add_argument("--rows-per-block", type=int, default=2, help="R of the sparse form for --sparse-only")
+    ap.add_argument("--split-only", type=int, default=0, metavar="M",
+                    help="time only the row-split product at m = M (profiling aid)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -477,6 +503,8 @@ def main() -> None:
     torch.cuda.set_device(local)
     if args.sparse_only:
         return run_sparse_only(rd, torch, args)
+    if args.split_only:
+        return run_split_only(rd, torch, args)
     dist = None
     if world > 1:
         import torch.distributed as dist
