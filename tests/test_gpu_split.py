@@ -308,3 +308,16 @@ def test_power_multi_mixes_split_and_sparse_runs(rd, torch_mod, orc, graph_steps
             assert n0 >= r["k"] and alpha % r["p"] == 0 and beta == r["q"] * (alpha // r["p"]), m
     for nn in range(3, 8):
         assert res[8]["gamma"][nn] == orc.row_dp(9, nn)
+
+
+@pytest.mark.parametrize("j", [1, 2, 5, 6])
+def test_power_split_every_split_point_m7(rd, torch_mod, orc, j):
+    """The period search through unbalanced splits (fibers of up to 1085 slots, metadata read from global
+    memory where it does not fit beside the rows) gives the oracle's relation and gamma sequence."""
+    m = 7
+    A, n = rd.transfer_matrix(m)
+    plan = rd.split_plan(m, j, x_ld=A.stride(0))
+    r = rd.power_until_periodic_split(A, plan, 40, rd.power_workspace(n, A.stride(0), 40, 8))
+    o = orc.power_until_periodic(m, kmax=40)
+    assert (r["k"], r["p"], r["q"]) == (o["k"], o["p"], o["q"])
+    assert np.array_equal(r["gamma"][1:r["j"] + 1], o["gamma"][1:o["j"] + 1])
