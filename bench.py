@@ -166,19 +166,24 @@ def time_to_period(rd, torch, ms: list[int], with_oracle: bool) -> dict:
         A = torch.empty((n, ld), dtype=torch.int16, device="cuda")
         rd.build_transfer(m, A)
         nnz = int((A[:, :n] != rd.RD_INF).sum().item())
-        # one untimed pass (first touch of allocations, module load), then the timed one
+        # one untimed pass (first touch of allocations, module load), then the timed one; N <= 128 runs
+        # the single-CTA search of rd_power_until_periodic (no plan), larger N the row-split step
+        small = n <= 128
         for _ in range(2):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             rd.build_transfer(m, A)
-            plan = rd.split_plan(m, x_ld=ld)
-            r = rd.power_until_periodic_split(A, plan, kmax, work)
+            if small:
+                r = rd.power_until_periodic(A, n, kmax, work)
+            else:
+                plan = rd.split_plan(m, x_ld=ld)
+                r = rd.power_until_periodic_split(A, plan, kmax, work)
             gam = [closed_form(r, nn) for nn in range(3, 1001)]
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
-            if _ == 0:
-                del plan
         products = r["j"] - 1
+        if small:
+            plan = rd.split_plan(m, x_ld=ld)  # for the product timed alone below
         info = plan["info"]
         C = torch.empty_like(A)
         rd.split_minplus(plan, A, C)
@@ -192,7 +197,9 @@ def time_to_period(rd, torch, ms: list[int], with_oracle: bool) -> dict:
         prod_ms = e0.elapsed_time(e1) / 3
         moved = (2 * n + 2 * info.x_rows) * n * 2
         entry = {"N": n, "nnz_A": nnz, "k": r["k"], "p": r["p"], "q": r["q"], "products": products, "gpu_s": dt,
-                 "step": f"row split j={info.j} (w {info.w1}/{info.w2}, slabs per CTA {info.k1}/{info.k2})",
+                 "step": ("single-CTA search (N <= 128)" if small else
+                          f"row split j={info.j} (w {info.w1}/{info.w2}, slabs per CTA {info.k1}/{info.k2})"),
+                 "us_per_power": dt / r["j"] * 1e6,
                  "split_product_ms": prod_ms, "split_x_rows": info.x_rows,
                  "split_product_GBps": moved / (prod_ms * 1e-3) / 1e9,
                  "split_product_frac_of_measured_hbm": moved / (prod_ms * 1e-3) / 1e9 / HBM_GBS,
@@ -241,6 +248,41 @@ def time_to_period(rd, torch, ms: list[int], with_oracle: bool) -> dict:
         out[f"m={m}"] = entry
         del work, A, plan
         torch.cuda.empty_cache()
+    return out
+
+
+def small_case(rd, torch, m: int = 3, kmax: int = 32, reps: int = 20) -> dict:
+    """The small case (m = 3, n = 3..30): microseconds per power and per search, A(G) built once.
+    'single_cta' is rd_power_until_periodic, whose whole search runs in one CTA for N <= 128; for
+    comparison the step kernels through rd_power_until_periodic_multi with one run, from a captured CUDA
+    graph ('graph', 16 steps per graph, capture and instantiation inside each call) or launched
+    directly ('direct', state read every 8 steps)."""
+    A, n = rd.transfer_matrix(m)
+    plan = rd.sparse_plan(A, n, n, 1)
+    work = rd.power_workspace(n, A.stride(0), kmax, 8)
+    runs = [(A, n, plan, work)]
+    out = {"m": m, "N": n}
+    res = rd.power_until_periodic(A, n, kmax, work)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        res = rd.power_until_periodic(A, n, kmax, work)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / reps
+    out["single_cta"] = {"s_per_search": dt, "us_per_power": dt / res["j"] * 1e6}
+    for name, gsteps in (("multi_graph", 16), ("multi_direct", 0)):
+        res = rd.power_until_periodic_multi(runs, 1, kmax, graph_steps=gsteps)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            res = rd.power_until_periodic_multi(runs, 1, kmax, graph_steps=gsteps)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / reps
+        r = res[0]
+        out[name] = {"s_per_search": dt, "us_per_power": dt / r["j"] * 1e6}
+        assert (r["k"], r["p"], r["q"]) == (res["k"], res["p"], res["q"])
+    out.update({"k": r["k"], "p": r["p"], "q": r["q"], "powers": r["j"],
+                "gamma_n3_to_30": [closed_form(res, nn) for nn in range(3, 31)]})
     return out
 
 
@@ -608,6 +650,7 @@ def main() -> None:
         extra["batched"] = batched_products(rd, torch)
     if rank == 0 and not args.no_period:
         extra["time_to_period"] = time_to_period(rd, torch, [3, 7, 9, 10], with_oracle=not args.no_cpu)
+        extra["small_case"] = small_case(rd, torch)
     if rank == 0 and not args.no_cpu:
         extra["cpu_baseline"] = cpu_baseline_gemm(a, b, rows=32)
 

@@ -172,7 +172,9 @@ rd_status rd_power_work_bytes(int64_t N, int64_t ld, int kmax, int slots, size_t
  * entries 1..kmax are valid), RD_ERR_RANGE (a normalised power left
  * [0, RD_MAX_FINITE]), RD_ERR_NOMEM (the ring was too short to hold the
  * matching power P_i), RD_ERR_ARG or RD_ERR_CUDA.  The call synchronises the
- * stream before returning; all host outputs are valid on return.
+ * stream before returning; all host outputs are valid on return.  For N <= 128
+ * the whole search runs in one CTA (one launch; the same work-buffer contents
+ * and results), also when reached through the _sparse and _split variants.
  */
 rd_status rd_power_until_periodic(const int16_t *A_dev, int64_t N, int64_t lda, int kmax, void *work_dev,
                                   size_t work_bytes, int64_t *gamma_host, int32_t *k_out, int32_t *p_out,

@@ -76,6 +76,159 @@ rd_status fail(cudaError_t e) {
   return RD_ERR_CUDA;
 }
 
+// ---------------------------------------------------------------- small matrices: one CTA per search
+//
+// For N <= kSmallN the whole search runs in one CTA with A, the current power and the next raw product
+// in shared memory (96 KB at N = 128): one launch and one host read per search instead of four
+// launches per power.  The CTA leaves the work area exactly as the step kernels do -- state header,
+// offsets, gamma, a hash per power, and each normalised power in its ring slot -- and follows the same
+// rules: P_1 = A - min A, P_{k+1} = (P_k (x) A) - mu, gamma_k = o_{k-1} + the raw diagonal minimum,
+// the operand contract and the range check, a hash match with a power that has left the ring is an
+// error (kErrRing), more than kMaxCand matches is an error, and the smallest exactly equal earlier power
+// ends the search.  The products are exact, so the result equals the large-matrix path's.
+constexpr int64_t kSmallN = 128;
+constexpr int kSmallThreads = 1024;
+
+size_t small_smem(int64_t N, int kmax) {
+  const size_t np = (size_t)((N + 7) / 8 * 8);
+  return 3 * (size_t)N * np * 2 + 8 * (size_t)(kmax + 1);
+}
+
+__global__ void __launch_bounds__(kSmallThreads) small_search_kernel(const int16_t* __restrict__ A, int64_t N,
+                                                                     int64_t lda, int kmax, PowerState* st,
+                                                                     int16_t* ring, int64_t slot_elems, int slots) {
+  extern __shared__ uint4 smq[];
+  __shared__ int32_t red[32];
+  __shared__ unsigned long long redh[32];
+  const int n = (int)N, np = (int)((N + 7) / 8 * 8), cells = n * np, half = np / 2;
+  int16_t* sA = reinterpret_cast<int16_t*>(smq);  // n x np, columns >= n are RD_INF
+  int16_t* sP = sA + cells;                       // the current normalised power
+  int16_t* sR = sP + cells;                       // the next raw product
+  unsigned long long* shash = reinterpret_cast<unsigned long long*>(sR + cells);  // a hash per power
+
+  init_state_body(st, kmax, slots);
+  for (int idx = threadIdx.x; idx < cells; idx += blockDim.x) {
+    const int i = idx / np, j = idx % np;
+    sA[idx] = (j < n) ? A[(int64_t)i * lda + j] : kInf;
+  }
+  __syncthreads();
+  int64_t* off = st_offset(st);
+  int64_t* gam = st_gamma(st);
+  unsigned long long* hs = st_hash(st);
+
+  for (int kn = 1; kn <= kmax; ++kn) {
+    const int16_t* src = sA;
+    if (kn > 1) {
+      // raw product R = P_{kn-1} (x) A: two columns per DPX add-min, the P entry in both halves
+      const uint32_t* a32 = reinterpret_cast<const uint32_t*>(sA);
+      for (int q = threadIdx.x; q < n * half; q += blockDim.x) {
+        const int i = q / half, jp = q % half;
+        const int16_t* prow = sP + i * np;
+        uint32_t acc = kInf2;
+        for (int t = 0; t < n; ++t) acc = __viaddmin_s16x2((uint32_t)(uint16_t)prow[t] * 0x00010001u, a32[t * half + jp], acc);
+        reinterpret_cast<uint32_t*>(sR)[q] = acc;
+      }
+      __syncthreads();
+      src = sR;
+    }
+    // min and diagonal minimum of the raw matrix; on the first power also the operand contract
+    int32_t lm = kInf, ldm = kInf;
+    int bad = 0;
+    for (int idx = threadIdx.x; idx < cells; idx += blockDim.x) {
+      const int i = idx / np, j = idx % np;
+      if (j >= n) continue;
+      const int32_t x = src[idx];
+      if (kn == 1) bad |= (x != kInf) && (x < 0 || x > kMaxFinite);
+      lm = min(lm, x);
+      if (i == j) ldm = min(ldm, x);
+    }
+    lm = block_reduce_min(lm, red);
+    ldm = block_reduce_min(ldm, red);
+    const int32_t mu = (lm >= kInf) ? 0 : lm;
+    // P_kn = raw - mu on finite entries, into shared memory and its ring slot, with its hash
+    int16_t* slot = ring + (int64_t)(kn % slots) * slot_elems;
+    unsigned long long h = 0;
+    for (int idx = threadIdx.x; idx < cells; idx += blockDim.x) {
+      const int i = idx / np, j = idx % np;
+      int32_t x = src[idx];
+      if (j < n) {
+        if (x != kInf) {
+          x -= mu;
+          bad |= (x < 0 || x > kMaxFinite);
+        }
+        slot[(int64_t)i * lda + j] = (int16_t)x;
+        h += mix64(((unsigned long long)idx << 16) ^ (unsigned long long)(uint16_t)x);
+      } else {
+        x = kInf;
+      }
+      sP[idx] = (int16_t)x;
+    }
+    h = block_reduce_sum(h, redh);
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+      off[kn] = off[kn - 1] + mu;
+      gam[kn] = (ldm >= kInf) ? RD_GAMMA_INF : off[kn - 1] + ldm;
+      hs[kn] = h;
+      shash[kn] = h;
+    }
+    if (bad) {
+      if (threadIdx.x == 0) {
+        st->err |= kErrRange;
+        st->done = 3;
+        st->k = kn - 1;
+      }
+      return;
+    }
+    __syncthreads();  // the slot and shash entries are visible to the whole CTA
+    // earlier powers with the same hash: one that has left the ring, or more than kMaxCand resident
+    // ones, is an error; otherwise the smallest resident one equal entry by entry ends the search
+    int err = 0, ncand = 0, found = -1;
+    for (int i = 1; i < kn; ++i) {
+      if (shash[i] != h) continue;
+      if (kn - i >= slots)
+        err |= kErrRing;
+      else if (++ncand > kMaxCand)
+        err |= kErrCandidates;
+    }
+    for (int i = 1; i < kn && found < 0 && !err; ++i) {
+      if (shash[i] != h) continue;
+      const int16_t* pi = ring + (int64_t)(i % slots) * slot_elems;
+      int diff = 0;
+      for (int idx = threadIdx.x; idx < cells; idx += blockDim.x) {
+        const int r = idx / np, c = idx % np;
+        if (c < n) diff |= (pi[(int64_t)r * lda + c] != sP[idx]);
+      }
+      if (!__syncthreads_or(diff)) found = i;
+    }
+    if (err) {
+      if (threadIdx.x == 0) {
+        st->err |= err;
+        st->done = 3;
+        st->k = kn - 1;
+      }
+      return;
+    }
+    if (found >= 1) {
+      if (threadIdx.x == 0) {
+        st->found_i = found;
+        st->found_j = kn;
+        st->found_q = off[kn] - off[found];
+        st->done = 1;
+        st->k = kn;
+      }
+      return;
+    }
+    if (kn >= kmax) {
+      if (threadIdx.x == 0) {
+        st->done = 2;
+        st->k = kn;
+      }
+      return;
+    }
+    __syncthreads();  // sP is read by the next product
+  }
+}
+
 }  // namespace
 
 // R = P_k (x) A with the DPX GEMM in ring mode.
@@ -97,6 +250,31 @@ cudaError_t dense_power_product(const Run& r, const void*, cudaStream_t s) {
   return launch_minplus_gemm(p, true, s);
 }
 
+namespace {
+// The host outputs of a finished search from its final state header and gamma array.
+rd_status search_outputs(const PowerState& h, void* work_dev, int kmax, int64_t* gamma_host, int32_t* k_out,
+                         int32_t* p_out, int64_t* q_out, cudaStream_t s) {
+  const int last = (h.done == 1) ? h.found_j : h.k;
+  cudaError_t e = cudaMemcpyAsync(gamma_host, reinterpret_cast<char*>(work_dev) + kStateHeader + 8 * (size_t)(kmax + 1),
+                                  8 * (size_t)(kmax + 1), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(e);
+  for (int k = 0; k <= kmax; ++k)
+    if (k < 1 || k > last) gamma_host[k] = RD_GAMMA_UNSET;
+  if (h.done == 1) {
+    *k_out = h.found_i;
+    *p_out = h.found_j - h.found_i;
+    *q_out = h.found_q;
+    return RD_OK;
+  }
+  *k_out = 0;
+  *p_out = 0;
+  *q_out = 0;
+  if (h.done == 3) return status_from_err(h.err);
+  return RD_NOT_FOUND;
+}
+}  // namespace
+
 // Algorithm 2 on a validated work area: state header, then the ring of powers.
 // No host heap use: the gamma table is copied straight into gamma_host.
 rd_status power_search(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, void* work_dev, size_t work_bytes,
@@ -114,13 +292,29 @@ rd_status power_search(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, v
   r.ld = lda;
   r.A = A_dev;
   r.grid = reduction_grid();
-  cudaError_t e = enqueue_first(r, kmax, s);
+  cudaError_t e = cudaSuccess;
+  PowerState h{};
+  if (N <= kSmallN) {
+    // one CTA runs the whole search (the product's operands A and P_k fit in shared memory)
+    const size_t smem = small_smem(N, kmax);
+    if (smem <= 200 * 1024) {
+      e = cudaFuncSetAttribute(small_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) {
+        small_search_kernel<<<1, kSmallThreads, smem, s>>>(A_dev, N, lda, kmax, r.st, r.ring, r.slot_elems, r.slots);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&h, r.st, sizeof(PowerState), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return fail(e);
+      return search_outputs(h, work_dev, kmax, gamma_host, k_out, p_out, q_out, s);
+    }
+  }
+  e = enqueue_first(r, kmax, s);
   if (e != cudaSuccess) return fail(e);
   // Steps per host check: large products are long enough that one check per
   // step costs nothing; small ones are batched (surplus steps exit at once).
   const int chunk = (N >= 2048) ? 1 : (N >= 512 ? 4 : 16);
   int enqueued = 1;
-  PowerState h{};
   for (;;) {
     e = cudaMemcpyAsync(&h, r.st, sizeof(PowerState), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -133,24 +327,7 @@ rd_status power_search(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, v
     }
     enqueued += n;
   }
-  const int last = (h.done == 1) ? h.found_j : h.k;
-  e = cudaMemcpyAsync(gamma_host, reinterpret_cast<char*>(work_dev) + kStateHeader + 8 * (size_t)(kmax + 1),
-                      8 * (size_t)(kmax + 1), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return fail(e);
-  for (int k = 0; k <= kmax; ++k)
-    if (k < 1 || k > last) gamma_host[k] = RD_GAMMA_UNSET;
-  if (h.done == 1) {
-    *k_out = h.found_i;
-    *p_out = h.found_j - h.found_i;
-    *q_out = h.found_q;
-    return RD_OK;
-  }
-  *k_out = 0;
-  *p_out = 0;
-  *q_out = 0;
-  if (h.done == 3) return status_from_err(h.err);
-  return RD_NOT_FOUND;
+  return search_outputs(h, work_dev, kmax, gamma_host, k_out, p_out, q_out, s);
 }
 
 }  // namespace rd
@@ -232,6 +409,15 @@ rd_status compute_cached(int m, Cached* out) {
   }
   if (rc == RD_OK) rc = rd_build_transfer(m, A, ld, s);
   const int split_j = rd_split_default_j(m);
+  if (rc == RD_OK && N <= kSmallN) {
+    // small matrices: the whole search in one CTA
+    rc = rd_power_until_periodic(A, N, ld, kGammaKmax, work, wbytes, g.data(), &k, &p, &q, s);
+    if (s) cudaStreamSynchronize(s);
+    if (A) cudaFree(A);
+    if (work) cudaFree(work);
+    if (s) cudaStreamDestroy(s);
+    return finish_cached(rc, g, k, p, q, out);
+  }
   if (rc == RD_OK && split_j > 0) {
     // the row-split step: A(G) (x) P_k from the row rules, in two passes
     size_t pbytes = 0;
