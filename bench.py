@@ -262,14 +262,14 @@ def small_case(rd, torch, m: int = 3, kmax: int = 32, reps: int = 20) -> dict:
     work = rd.power_workspace(n, A.stride(0), kmax, 8)
     runs = [(A, n, plan, work)]
     out = {"m": m, "N": n}
-    res = rd.power_until_periodic(A, n, kmax, work)
+    single = rd.power_until_periodic(A, n, kmax, work)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(reps):
-        res = rd.power_until_periodic(A, n, kmax, work)
+        single = rd.power_until_periodic(A, n, kmax, work)
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / reps
-    out["single_cta"] = {"s_per_search": dt, "us_per_power": dt / res["j"] * 1e6}
+    out["single_cta"] = {"s_per_search": dt, "us_per_power": dt / single["j"] * 1e6}
     for name, gsteps in (("multi_graph", 16), ("multi_direct", 0)):
         res = rd.power_until_periodic_multi(runs, 1, kmax, graph_steps=gsteps)  # warm-up
         torch.cuda.synchronize()
@@ -280,9 +280,9 @@ def small_case(rd, torch, m: int = 3, kmax: int = 32, reps: int = 20) -> dict:
         dt = (time.perf_counter() - t0) / reps
         r = res[0]
         out[name] = {"s_per_search": dt, "us_per_power": dt / r["j"] * 1e6}
-        assert (r["k"], r["p"], r["q"]) == (res["k"], res["p"], res["q"])
-    out.update({"k": r["k"], "p": r["p"], "q": r["q"], "powers": r["j"],
-                "gamma_n3_to_30": [closed_form(res, nn) for nn in range(3, 31)]})
+        assert (r["k"], r["p"], r["q"]) == (single["k"], single["p"], single["q"])
+    out.update({"k": single["k"], "p": single["p"], "q": single["q"], "powers": single["j"],
+                "gamma_n3_to_30": [closed_form(single, nn) for nn in range(3, 31)]})
     return out
 
 
