@@ -301,7 +301,11 @@ rd_status rd_sparse_tune(const int16_t *A, int64_t lda, int64_t N, void *scratch
  *            pass 1, finite rows of X of one pi in pass 2);
  *   lmax1, lmax2    list entries of one fiber at most (staged with it);
  *   k1, k2   column slabs one CTA sweeps per fiber (1..64, default 8; a
- *            caller may change them like w1, w2).
+ *            caller may change them like w1, w2);
+ *   chunk_cols  0 (default): both passes run over all N columns, X has
+ *            x_rows x N entries; > 0 (a multiple of 128): they run chunk by
+ *            chunk of that many columns and X holds one chunk (x_rows x
+ *            chunk_cols), so X can stay in L2 between the two passes.
  */
 typedef struct {
   int32_t m, j;
@@ -314,6 +318,7 @@ typedef struct {
   int32_t slots1, slots2;
   int32_t lmax1, lmax2;
   int32_t k1, k2;
+  int32_t chunk_cols;
 } rd_split_info_t;
 
 /* rd_split_default_j -- the split used by default, floor(m / 2); 0 when m is
@@ -341,8 +346,8 @@ rd_status rd_split_plan(int m, int j, void *plan_dev, size_t plan_bytes, rd_spli
  * rd_split_minplus -- C = A(G) (x) B for the m of the plan, entries of B in
  * [0, RD_MAX_FINITE] or RD_INF.  B (N x N, ldb), C (N x N, ldc) and the
  * intermediate X_dev (info->x_rows x ldx int16) are caller-owned device
- * buffers, 16-byte aligned, leading dimensions multiples of 8 and >= N; X is
- * overwritten.  Columns N..ld-1 of C are not written.  min_out (nullable,
+ * buffers, 16-byte aligned, leading dimensions multiples of 8, ldb and ldc
+ * >= N, ldx >= N (or >= info->chunk_cols when that is set); X is overwritten.  Columns N..ld-1 of C are not written.  min_out (nullable,
  * device int32): set to min C, RD_INF if all entries are RD_INF.  Asynchronous
  * on s.  RD_ERR_ARG for an invalid plan description or operand.
  */

@@ -402,7 +402,8 @@ class SplitInfo(ctypes.Structure):
                 ("list1_entries", ctypes.c_int64), ("list2_entries", ctypes.c_int64), ("x_rows", ctypes.c_int64),
                 ("plan_bytes", ctypes.c_uint64), ("w1", ctypes.c_int32), ("w2", ctypes.c_int32),
                 ("slots1", ctypes.c_int32), ("slots2", ctypes.c_int32), ("lmax1", ctypes.c_int32),
-                ("lmax2", ctypes.c_int32), ("k1", ctypes.c_int32), ("k2", ctypes.c_int32)]
+                ("lmax2", ctypes.c_int32), ("k1", ctypes.c_int32), ("k2", ctypes.c_int32),
+                ("chunk_cols", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -419,8 +420,10 @@ def split_plan_bytes(m: int, j: int) -> int:
     return out.value
 
 
-def split_plan(m: int, j: int | None = None, device="cuda", x_ld: int | None = None, stream=None) -> dict:
-    """Allocate (torch) and build the row-split plan of A(G) for m rows, plus its intermediate X."""
+def split_plan(m: int, j: int | None = None, device="cuda", x_ld: int | None = None, chunk_cols: int = 0,
+               stream=None) -> dict:
+    """Allocate (torch) and build the row-split plan of A(G) for m rows, plus its intermediate X
+    (all N columns, or one chunk of chunk_cols columns)."""
     import torch
 
     j = split_default_j(m) if j is None else j
@@ -428,7 +431,8 @@ def split_plan(m: int, j: int | None = None, device="cuda", x_ld: int | None = N
     info = SplitInfo()
     _check(_lib().rd_split_plan(m, j, _dptr(plan), plan.numel(), ctypes.byref(info), _stream(stream)),
            "rd_split_plan")
-    ld = padded_dim(info.N) if x_ld is None else x_ld
+    info.chunk_cols = chunk_cols
+    ld = (chunk_cols if chunk_cols else padded_dim(info.N)) if x_ld is None else x_ld
     X = torch.empty((info.x_rows, ld), dtype=torch.int16, device=device)
     return dict(info=info, plan=plan, X=X)
 

@@ -497,7 +497,8 @@ struct SplitPass {
   int64_t ldin;
   int16_t* out;  // pass 1: X;  pass 2: R
   int64_t ldout;
-  int64_t ncols;
+  int64_t ncols;           // columns of this launch (a chunk of the N columns)
+  int64_t in_col0, out_col0;  // first column of the chunk in `in` resp. `out` (X holds one chunk at column 0)
   int32_t n_groups;
   int32_t max_slots;      // shared-memory rows = max_slots + 1 (row 0 is the dummy)
   int32_t max_list;       // list entries of one fiber at most
@@ -585,6 +586,8 @@ __global__ void __launch_bounds__(kSplitThreads) split_pass_kernel(SplitPass a) 
     else
       out = a.ring + (int64_t)((k + 1) % a.slots) * a.slot_elems;
   }
+  in += a.in_col0;
+  out += a.out_col0;
   const int lane = threadIdx.x % LR, gi = threadIdx.x / LR;
   const int64_t f = blockIdx.y;
   const uint4 inf4 = make_uint4(kInf2, kInf2, kInf2, kInf2);
@@ -711,8 +714,8 @@ __global__ void __launch_bounds__(kSplitThreads) split_pass_kernel(SplitPass a) 
               }
             }
           }
-          if ((uint64_t)(row - c) < 8) {
-            const int e = (int)(row - c);
+          if ((uint64_t)(row - a.out_col0 - c) < 8) {
+            const int e = (int)(row - a.out_col0 - c);
             ldiag = min(ldiag, (int32_t)((w4[e >> 1] >> (16 * (e & 1))) & 0xFFFFu));
           }
         }
@@ -835,6 +838,25 @@ cudaError_t launch_pass(const SplitPass& a, int W, int64_t fibers, cudaStream_t 
   return cudaGetLastError();
 }
 
+// Both passes over the columns in chunks of info.chunk_cols (all N at once when 0): X holds one chunk.
+template <bool RING>
+cudaError_t run_passes(SplitPass p1, SplitPass p2, const rd_split_info_t& info, cudaStream_t s) {
+  const int64_t N = info.N;
+  const int64_t cw = info.chunk_cols > 0 ? info.chunk_cols : N;
+  cudaError_t e = cudaSuccess;
+  for (int64_t c0 = 0; c0 < N && e == cudaSuccess; c0 += cw) {
+    const int64_t w = (N - c0 < cw) ? (N - c0) : cw;
+    p1.ncols = p2.ncols = w;
+    p1.in_col0 = c0;
+    p1.out_col0 = 0;
+    p2.in_col0 = 0;
+    p2.out_col0 = c0;
+    e = launch_pass<true, RING>(p1, info.w1, info.n_sigma, s);
+    if (e == cudaSuccess) e = launch_pass<false, RING>(p2, info.w2, info.n_pi, s);
+  }
+  return e;
+}
+
 // The two passes' fixed operands, from a built plan.
 void passes_of(const rd_split_info_t& info, const void* plan, SplitPass* p1, SplitPass* p2) {
   Layout L;
@@ -873,13 +895,16 @@ bool info_ok(const rd_split_info_t* info, const void* plan) {
   if (info->x_rows < 1 || info->x_rows > (int64_t)L.nPi * info->n_sigma) return false;
   if (info->lmax1 < 0 || info->lmax2 < 0 || info->k1 < 1 || info->k1 > 64 || info->k2 < 1 || info->k2 > 64)
     return false;
+  if (info->chunk_cols < 0 || info->chunk_cols % 128 != 0) return false;
   return valid_w(info->w1, info->slots1) && valid_w(info->w2, info->slots2);
 }
 
+// Columns X must hold: one chunk, or all N.
+int64_t x_cols(const rd_split_info_t& info) { return info.chunk_cols > 0 ? info.chunk_cols : info.N; }
+
 struct SplitCtx {
   SplitPass p1, p2;
-  int w1, w2;
-  int64_t fibers1, fibers2;
+  rd_split_info_t info;
 };
 
 cudaError_t split_power_product(const Run& r, const void* ctx, cudaStream_t s) {
@@ -893,9 +918,7 @@ cudaError_t split_power_product(const Run& r, const void* ctx, cudaStream_t s) {
   p2.ldout = r.ld;
   p2.min_out = &r.st->mu;
   p2.diag_out = &r.st->dmin;
-  cudaError_t e = launch_pass<true, true>(p1, c->w1, c->fibers1, s);
-  if (e == cudaSuccess) e = launch_pass<false, true>(p2, c->w2, c->fibers2, s);
-  return e;
+  return run_passes<true>(p1, p2, c->info, s);
 }
 
 rd_status fail(cudaError_t e) {
@@ -906,7 +929,7 @@ rd_status fail(cudaError_t e) {
 }  // namespace
 
 bool split_ring_ok(const SplitRing& d, int64_t N) {
-  return info_ok(&d.info, d.plan) && d.info.N == N && d.X != nullptr && aligned16(d.X) && d.ldx >= N &&
+  return info_ok(&d.info, d.plan) && d.info.N == N && d.X != nullptr && aligned16(d.X) && d.ldx >= x_cols(d.info) &&
          d.ldx % 8 == 0;
 }
 
@@ -918,10 +941,7 @@ cudaError_t split_ring_product(const SplitRing& d, PowerState* st, int16_t* ring
   c.p1.ldout = d.ldx;
   c.p2.in = d.X;
   c.p2.ldin = d.ldx;
-  c.w1 = d.info.w1;
-  c.w2 = d.info.w2;
-  c.fibers1 = d.info.n_sigma;
-  c.fibers2 = d.info.n_pi;
+  c.info = d.info;
   Run r{};
   r.st = st;
   r.ring = ring;
@@ -1120,6 +1140,7 @@ extern "C" rd_status rd_split_plan(int m, int j, void* plan_dev, size_t plan_byt
   info->lmax2 = lm[1];
   info->k1 = kDefaultSlabsPerCta;
   info->k2 = kDefaultSlabsPerCta;
+  info->chunk_cols = 0;
   return RD_OK;
 }
 
@@ -1128,7 +1149,7 @@ extern "C" rd_status rd_split_minplus(const rd_split_info_t* info, const void* p
                                       int32_t* min_out, cudaStream_t s) {
   if (!info_ok(info, plan_dev) || !B || !X_dev || !C) return RD_ERR_ARG;
   const int64_t N = info->N;
-  if (ldb < N || ldb % 8 != 0 || ldx < N || ldx % 8 != 0 || ldc < N || ldc % 8 != 0) return RD_ERR_ARG;
+  if (ldb < N || ldb % 8 != 0 || ldx < x_cols(*info) || ldx % 8 != 0 || ldc < N || ldc % 8 != 0) return RD_ERR_ARG;
   if (!aligned16(B) || !aligned16(X_dev) || !aligned16(C)) return RD_ERR_ARG;
   cudaError_t e = cudaSuccess;
   if (min_out) {
@@ -1146,8 +1167,7 @@ extern "C" rd_status rd_split_minplus(const rd_split_info_t* info, const void* p
   p2.out = C;
   p2.ldout = ldc;
   p2.min_out = min_out;
-  e = launch_pass<true, false>(p1, info->w1, info->n_sigma, s);
-  if (e == cudaSuccess) e = launch_pass<false, false>(p2, info->w2, info->n_pi, s);
+  e = run_passes<false>(p1, p2, *info, s);
   if (e != cudaSuccess) return fail(e);
   return RD_OK;
 }
@@ -1159,7 +1179,8 @@ extern "C" rd_status rd_power_until_periodic_split(const int16_t* A_dev, int64_t
   if (!A_dev || !info_ok(info, plan_dev) || !X_dev || !work_dev || !gamma_host || !k_out || !p_out || !q_out)
     return RD_ERR_ARG;
   const int64_t N = info->N;
-  if (lda < N || lda % 8 != 0 || ldx < N || ldx % 8 != 0 || kmax < 1 || kmax > (1 << 20)) return RD_ERR_ARG;
+  if (lda < N || lda % 8 != 0 || ldx < x_cols(*info) || ldx % 8 != 0 || kmax < 1 || kmax > (1 << 20))
+    return RD_ERR_ARG;
   if (!aligned16(A_dev) || !aligned16(X_dev) || (reinterpret_cast<uintptr_t>(work_dev) & 255u) != 0)
     return RD_ERR_ARG;
   SplitCtx c{};
@@ -1168,10 +1189,7 @@ extern "C" rd_status rd_power_until_periodic_split(const int16_t* A_dev, int64_t
   c.p1.ldout = ldx;
   c.p2.in = X_dev;
   c.p2.ldin = ldx;
-  c.w1 = info->w1;
-  c.w2 = info->w2;
-  c.fibers1 = info->n_sigma;
-  c.fibers2 = info->n_pi;
+  c.info = *info;
   return power_search(A_dev, N, lda, kmax, work_dev, work_bytes, split_power_product, &c, gamma_host, k_out, p_out,
                       q_out, s);
 }

@@ -321,3 +321,30 @@ def test_power_split_every_split_point_m7(rd, torch_mod, orc, j):
     o = orc.power_until_periodic(m, kmax=40)
     assert (r["k"], r["p"], r["q"]) == (o["k"], o["p"], o["q"])
     assert np.array_equal(r["gamma"][1:r["j"] + 1], o["gamma"][1:o["j"] + 1])
+
+
+@pytest.mark.parametrize("chunk", [128, 384, 1024])
+def test_split_column_chunks(rd, torch_mod, orc, chunk):
+    """chunk_cols > 0: both passes run chunk by chunk with X holding one chunk (ragged last chunk
+    included); the product and the period search equal the oracle's."""
+    torch = torch_mod
+    from paper_2409_17658_gb300 import inputs
+
+    m = 6
+    n = rd.state_count(m)
+    b = inputs.matrix(n, n, seed=111, dist="wide")
+    B = upload(torch, b, junk=-5)
+    plan = rd.split_plan(m, chunk_cols=chunk)
+    assert plan["X"].shape[1] == chunk
+    C = torch.full((n, B.stride(0)), 777, dtype=torch.int16, device="cuda")
+    mn = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rd.split_minplus(plan, B, C, min_out=mn)
+    want = orc.minplus_i16(to_i16(orc.transfer(m)), b)
+    got = C.cpu().numpy()
+    assert np.array_equal(got[:, :n].astype(np.int32), want)
+    assert np.all(got[:, n:] == 777) and mn.item() == want.min()
+    A, _ = rd.transfer_matrix(m)
+    r = rd.power_until_periodic_split(A, plan, 40, rd.power_workspace(n, A.stride(0), 40, 8))
+    o = orc.power_until_periodic(m, kmax=40)
+    assert (r["k"], r["p"], r["q"]) == (o["k"], o["p"], o["q"])
+    assert np.array_equal(r["gamma"][1:r["j"] + 1], o["gamma"][1:o["j"] + 1])
