@@ -60,12 +60,13 @@ cudaError_t enqueue_first(const Run& r, int kmax, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// One power step: the product (dense or sparse), then normalise/hash, finalize, compare.
-cudaError_t enqueue_step(const Run& r, ProductFn product, const void* ctx, cudaStream_t s) {
+// One power step: the product, then normalise/hash (unless the product did it), finalize, compare.
+cudaError_t enqueue_step(const Run& r, ProductFn product, const void* ctx, bool normalised, cudaStream_t s) {
   cudaError_t e = product(r, ctx, s);
   if (e != cudaSuccess) return e;
-  normalise_hash_kernel<false><<<r.grid, kRedThreads, 0, s>>>(nullptr, r.st, r.ring, r.slot_elems, r.slots, r.N,
-                                                               r.ld);
+  if (!normalised)
+    normalise_hash_kernel<false><<<r.grid, kRedThreads, 0, s>>>(nullptr, r.st, r.ring, r.slot_elems, r.slots, r.N,
+                                                                 r.ld);
   finalize_kernel<<<1, 32, 0, s>>>(r.st);
   compare_resolve_kernel<<<r.grid, kRedThreads, 0, s>>>(r.st, r.ring, r.slot_elems, r.slots, r.N, r.ld);
   return cudaGetLastError();
@@ -279,7 +280,7 @@ rd_status search_outputs(const PowerState& h, void* work_dev, int kmax, int64_t*
 // No host heap use: the gamma table is copied straight into gamma_host.
 rd_status power_search(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, void* work_dev, size_t work_bytes,
                        ProductFn product, const void* ctx, int64_t* gamma_host, int32_t* k_out, int32_t* p_out,
-                       int64_t* q_out, cudaStream_t s) {
+                       int64_t* q_out, cudaStream_t s, bool normalised) {
   const size_t sb = state_bytes(kmax), pb = slot_bytes(N, lda);
   if (work_bytes < sb + 2 * pb) return RD_ERR_NOMEM;
   const size_t slots64 = (work_bytes - sb) / pb;
@@ -322,7 +323,7 @@ rd_status power_search(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, v
     if (h.done || enqueued >= kmax) break;
     const int n = (kmax - enqueued < chunk) ? (kmax - enqueued) : chunk;
     for (int i = 0; i < n; ++i) {
-      e = enqueue_step(r, product, ctx, s);
+      e = enqueue_step(r, product, ctx, normalised, s);
       if (e != cudaSuccess) return fail(e);
     }
     enqueued += n;

@@ -31,6 +31,7 @@ struct MultiRun {
   const uint32_t* rec;
   int64_t nb, slabs;
   const SplitRing* split;  // non-null: this run's product is the row-split step
+  int32_t normalised;      // its product writes the normalised power (no normaliser pass)
 };
 
 struct MultiParams {
@@ -59,6 +60,7 @@ __global__ void multi_reduce_kernel(const __grid_constant__ MultiParams mp) {
 template <bool COPY>
 __global__ void multi_normalise_kernel(const __grid_constant__ MultiParams mp) {
   const MultiRun& q = mp.r[blockIdx.y];
+  if (!COPY && q.normalised) return;  // the row-split product wrote the normalised power itself
   normalise_hash_body<COPY>(q.A, q.st, q.ring, q.slot_elems, q.slots, q.N, q.ld);
 }
 
@@ -197,6 +199,7 @@ static void fill_params(const RunDesc* runs, int count, int R, MultiParams* mp) 
     q.start = d.start;
     q.rec = d.rec;
     q.split = d.split;
+    q.normalised = (d.split != nullptr && split_normalises(d.split->info)) ? 1 : 0;
     q.nb = (d.N + R - 1) / R;
     q.slabs = (d.N + kMultiThreads * 16 - 1) / (kMultiThreads * 16);
     if (d.N < kOwnLaunchN && d.split == nullptr) {
@@ -269,6 +272,7 @@ extern "C" rd_status rd_power_until_periodic_multi(rd_power_run* runs, int count
     q.start = u.block_start;
     q.rec = u.records;
     q.split = split ? &split_rings[i] : nullptr;
+    q.normalised = (split && split_normalises(split_rings[i].info)) ? 1 : 0;
     q.nb = (u.N + R - 1) / R;
     q.slabs = (u.N + kMultiThreads * 16 - 1) / (kMultiThreads * 16);
     if (u.N < kOwnLaunchN && !split) {

@@ -99,12 +99,16 @@ typedef cudaError_t (*ProductFn)(const Run& r, const void* ctx, cudaStream_t s);
 
 cudaError_t dense_power_product(const Run& r, const void* ctx, cudaStream_t s);
 
+// `normalised`: the product itself writes the normalised power, its hash and range flag into the
+// state (the row-split step), so the normaliser pass is skipped.
 rd_status power_search(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, void* work_dev, size_t work_bytes,
                        ProductFn product, const void* ctx, int64_t* gamma_host, int32_t* k_out, int32_t* p_out,
-                       int64_t* q_out, cudaStream_t s);
+                       int64_t* q_out, cudaStream_t s, bool normalised = false);
 
 // A built row-split plan with its intermediate (split.cu), and the ring-mode product it runs: the
-// next raw power R = A(G) (x) P_k into the slot of power st->k + 1, min and diag-min into st.
+// next power A(G) (x) P_k, already normalised, into the slot of power st->k + 1, with its minimum
+// (the offset step), raw diagonal minimum, hash and range flag in st -- everything the normaliser
+// pass would add, so runs stepped by it skip that pass.
 struct SplitRing {
   rd_split_info_t info;
   const void* plan;
@@ -112,6 +116,7 @@ struct SplitRing {
   int64_t ldx;
 };
 bool split_ring_ok(const SplitRing& d, int64_t N);
+bool split_normalises(const rd_split_info_t& info);  // the ring product writes the normalised power
 cudaError_t split_ring_product(const SplitRing& d, PowerState* st, int16_t* ring, int64_t slot_elems, int slots,
                                int64_t ld, cudaStream_t s);
 
@@ -127,6 +132,7 @@ struct RunDesc {
   const uint32_t* rec;
   int64_t nb_unused, slabs_unused;  // filled in by the launcher
   const SplitRing* split;           // non-null: the row-split step instead of the sparse one
+  int32_t normalised;               // the product writes the normalised power (no normaliser pass)
 };
 constexpr int kMaxRunsPerStep = 16;
 cudaError_t runs_first(const RunDesc* runs, int count, int R, int kmax, cudaStream_t s);

@@ -38,6 +38,7 @@
 // reads them from global memory instead.
 #include <mutex>
 
+#include "power_dev.cuh"
 #include "rd_internal.cuh"
 
 namespace rd {
@@ -500,6 +501,8 @@ struct SplitPass {
   int64_t ncols;           // columns of this launch (a chunk of the N columns)
   int64_t in_col0, out_col0;  // first column of the chunk in `in` resp. `out` (X holds one chunk at column 0)
   int32_t n_groups;
+  int32_t norm;           // ring mode: pass 1 reduces the next offset step mu into st->mu, pass 2 writes
+                          // the power normalised by it, with its hash and range flag (no normaliser pass)
   int32_t max_slots;      // shared-memory rows = max_slots + 1 (row 0 is the dummy)
   int32_t max_list;       // list entries of one fiber at most
   int32_t slabs_per_cta;  // column slabs one CTA sweeps with its fiber staged once
@@ -622,6 +625,15 @@ __global__ void __launch_bounds__(kSplitThreads) split_pass_kernel(SplitPass a) 
   const uint32_t* pairs = STAGED ? slst : glst;
   int32_t lmin = kInf, ldiag = kInf;
   uint32_t m2 = kInf2;  // halfword minima of the full vectors written (pass 2)
+  uint32_t mv = kInf2;  // pass 1 with norm: halfword minima of the staged values
+  unsigned long long hsum = 0;  // pass 2 with norm: hash of the normalised power (as the normaliser's)
+  uint32_t nbad = 0;            // pass 2 with norm: a normalised entry left [0, RD_MAX_FINITE]
+  int32_t mu = 0;
+  if (RING && !FIRST && a.norm) {
+    const int32_t mr = *(volatile const int32_t*)&a.st->mu;  // complete: pass 1 has finished
+    mu = (mr >= kInf) ? 0 : mr;
+  }
+  const uint32_t mu2 = (uint32_t)mu * 0x00010001u;
 
   const int64_t slabs = (a.ncols + W - 1) / W;
   const int64_t sb_end = min(slabs, (int64_t)(blockIdx.x + 1) * a.slabs_per_cta);
@@ -652,6 +664,12 @@ __global__ void __launch_bounds__(kSplitThreads) split_pass_kernel(SplitPass a) 
             const uint32_t w2 = (uint32_t)(e[u] & 31) * 0x00010001u;
             v[u] = make_uint4(__viaddmin_s16x2(x.x, w2, kInf2), __viaddmin_s16x2(x.y, w2, kInf2),
                               __viaddmin_s16x2(x.z, w2, kInf2), __viaddmin_s16x2(x.w, w2, kInf2));
+            if (RING && a.norm) {
+              // min of A(G) (x) P = min over p, x of w(p) + P[p][x] (every word has a predecessor)
+              uint32_t t[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+              if (c + 8 > a.ncols) mask_tail(t, (int)(a.ncols - c));  // lanes past the chunk / N
+              mv = min3(min3(mv, t[0], t[1]), min3(t[2], t[3], kInf2), kInf2);
+            }
           } else {
             v[u] = __ldg(reinterpret_cast<const uint4*>(in + (int64_t)e[u] * a.ldin + c));
           }
@@ -700,7 +718,30 @@ __global__ void __launch_bounds__(kSplitThreads) split_pass_kernel(SplitPass a) 
         if (FIRST) {
           *reinterpret_cast<uint4*>(out + row * a.ldout + c) = acc[l];
         } else {
-          const uint32_t w4[4] = {acc[l].x, acc[l].y, acc[l].z, acc[l].w};
+          uint32_t w4[4] = {acc[l].x, acc[l].y, acc[l].z, acc[l].w};
+          if ((uint64_t)(row - a.out_col0 - c) < 8) {  // diagonal minimum of the raw product
+            const int e = (int)(row - a.out_col0 - c);
+            ldiag = min(ldiag, (int32_t)((w4[e >> 1] >> (16 * (e & 1))) & 0xFFFFu));
+          }
+          if (RING && a.norm) {
+            // P = R - mu on finite entries, range-checked, hashed per 16-byte chunk as the normaliser does
+            uint32_t hw[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const uint32_t isinf = __vcmpeq2(w4[q], kInf2);
+              const uint32_t sub = __vsub2(w4[q], mu2) & ~isinf;
+              hw[q] = sub | (kInf2 & isinf);
+            }
+            const int valid = (c + 8 <= a.ncols) ? 8 : (int)(a.ncols - c);
+            uint32_t chk[4] = {hw[0], hw[1], hw[2], hw[3]};
+            if (valid < 8) mask_tail(chk, valid);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) nbad |= __vcmpgtu2(chk[q], 0x1FFF1FFFu) & ~__vcmpeq2(chk[q], kInf2);
+            hsum += chunk_hash(row, a.out_col0 + c, chk);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w4[q] = hw[q];
+            acc[l] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          }
           if (c + 8 <= a.ncols) {
             *reinterpret_cast<uint4*>(out + row * a.ldout + c) = acc[l];
             m2 = min3(min3(m2, acc[l].x, acc[l].y), acc[l].z, acc[l].w);
@@ -714,11 +755,33 @@ __global__ void __launch_bounds__(kSplitThreads) split_pass_kernel(SplitPass a) 
               }
             }
           }
-          if ((uint64_t)(row - a.out_col0 - c) < 8) {
-            const int e = (int)(row - a.out_col0 - c);
-            ldiag = min(ldiag, (int32_t)((w4[e >> 1] >> (16 * (e & 1))) & 0xFFFFu));
-          }
         }
+      }
+    }
+  }
+
+  if (RING && a.norm) {
+    __shared__ unsigned long long red_h[kSplitThreads / 32];
+    __shared__ int32_t red_v[kSplitThreads / 32];
+    if (FIRST) {
+      int32_t v = (int32_t)min(mv & 0xFFFFu, mv >> 16);
+      for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+      if ((threadIdx.x & 31) == 0) red_v[threadIdx.x >> 5] = v;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int32_t bm = kInf;
+        for (int w = 0; w < kSplitThreads / 32; ++w) bm = min(bm, red_v[w]);
+        if (bm < kInf && bm < *(volatile const int32_t*)&a.st->mu) atomicMin(&a.st->mu, bm);
+      }
+    } else {
+      for (int o = 16; o > 0; o >>= 1) hsum += __shfl_xor_sync(0xFFFFFFFFu, hsum, o);
+      if ((threadIdx.x & 31) == 0) red_h[threadIdx.x >> 5] = hsum;
+      const int any_bad = __syncthreads_or(nbad != 0);
+      if (threadIdx.x == 0) {
+        unsigned long long h = 0;
+        for (int w = 0; w < kSplitThreads / 32; ++w) h += red_h[w];
+        atomicAdd(&a.st->hacc, h);
+        if (any_bad) atomicOr(&a.st->range_bad, 1);
       }
     }
   }
@@ -916,7 +979,10 @@ cudaError_t split_power_product(const Run& r, const void* ctx, cudaStream_t s) {
   p1.slots = p2.slots = r.slots;
   p1.ldin = r.ld;
   p2.ldout = r.ld;
-  p2.min_out = &r.st->mu;
+  // Unchunked, pass 1 sees every entry before pass 2 starts and reduces the offset step itself, and
+  // pass 2 writes the normalised power; in column chunks the normaliser pass does it after both.
+  p1.norm = p2.norm = split_normalises(c->info) ? 1 : 0;
+  p2.min_out = p2.norm ? nullptr : &r.st->mu;
   p2.diag_out = &r.st->dmin;
   return run_passes<true>(p1, p2, c->info, s);
 }
@@ -927,6 +993,8 @@ rd_status fail(cudaError_t e) {
 }
 
 }  // namespace
+
+bool split_normalises(const rd_split_info_t& info) { return info.chunk_cols == 0; }
 
 bool split_ring_ok(const SplitRing& d, int64_t N) {
   return info_ok(&d.info, d.plan) && d.info.N == N && d.X != nullptr && aligned16(d.X) && d.ldx >= x_cols(d.info) &&
@@ -1191,5 +1259,5 @@ extern "C" rd_status rd_power_until_periodic_split(const int16_t* A_dev, int64_t
   c.p2.ldin = ldx;
   c.info = *info;
   return power_search(A_dev, N, lda, kmax, work_dev, work_bytes, split_power_product, &c, gamma_host, k_out, p_out,
-                      q_out, s);
+                      q_out, s, split_normalises(*info));
 }
