@@ -120,7 +120,9 @@ rd_status rd_minplus_gemm(const int16_t *A, int64_t lda, const int16_t *B, int64
  * entries, device, any alignment) with a K x N matrix B (ldb): y[j] =
  * min_k x[k] + B[k][j], y device (16-byte aligned), N entries; conventions and
  * min_out as rd_minplus_gemm.  B is read once, so this is bound by HBM
- * bandwidth; rd_minplus_gemm uses it when M = 1.
+ * bandwidth; rd_minplus_gemm uses it when M = 1.  For N >= 4096 it runs as
+ * thread-block clusters of 8 CTAs (one 256-column band each) whose partial
+ * minima meet in distributed shared memory; no workspace.
  */
 rd_status rd_minplus_gemv(const int16_t *x, const int16_t *B, int64_t ldb, int16_t *y, int64_t N, int64_t K,
                           int32_t *min_out, cudaStream_t s);

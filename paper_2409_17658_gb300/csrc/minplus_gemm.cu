@@ -23,6 +23,8 @@
 //  * No overflow: operands lie in [0, 0x1FFF] or are 0x3FFF, so every sum is at
 //    most 0x7FFE; accumulators start at RD_INF and only decrease, so an entry
 //    whose terms all involve RD_INF ends exactly at RD_INF.
+#include <cooperative_groups.h>
+
 #include "rd_internal.cuh"
 
 namespace rd {
@@ -500,6 +502,119 @@ extern "C" rd_status rd_minplus_gemm(const int16_t* A, int64_t lda, const int16_
   return RD_OK;
 }
 
+// ---- the same product by clusters: a cluster of kGvRanks CTAs owns a band of kGvBand columns and
+// splits the rows between its CTAs; in a CTA each warp streams whole 512-byte row segments of the band
+// (one 16-byte load per lane, four rows in flight), so B is read in long contiguous runs.  The warps'
+// partial minima are combined in shared memory, then the CTAs' across the cluster through distributed
+// shared memory: CTA r of the cluster finishes 4 of the band's 32 vectors and writes them.  No
+// workspace and no atomics on y; the cluster barriers are hardware barriers (no polling).
+constexpr int kGvBand = 256, kGvThreads = 256, kGvRanks = 8, kGvXChunk = 4096, kGvUnroll = 4;
+constexpr int kGvWarps = kGvThreads / 32, kGvVecs = kGvBand / 8;
+
+__global__ void __launch_bounds__(kGvThreads) minplus_gemv_cluster_kernel(const int16_t* __restrict__ x,
+                                                                          const int16_t* __restrict__ B,
+                                                                          int64_t ldb, int16_t* __restrict__ y,
+                                                                          int64_t N, int64_t K, int32_t* min_out) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ uint32_t xs[kGvXChunk];
+  __shared__ uint4 part[kGvWarps][kGvVecs];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rank = (int)cluster.block_rank();
+  const int64_t col = (int64_t)blockIdx.x * kGvBand + lane * 8;
+  const bool full = col + 8 <= N, any = col < N;
+  // this CTA's rows
+  const int64_t per = (K + kGvRanks - 1) / kGvRanks;
+  const int64_t r0 = (int64_t)rank * per, r1 = (r0 + per < K) ? r0 + per : K;
+  uint32_t acc[4] = {kInf2, kInf2, kInf2, kInf2};
+  for (int64_t k0 = r0; k0 < r1; k0 += kGvXChunk) {
+    const int kc = (r1 - k0 < kGvXChunk) ? (int)(r1 - k0) : kGvXChunk;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kc; i += kGvThreads) xs[i] = (uint32_t)(uint16_t)x[k0 + i] * 0x00010001u;
+    __syncthreads();
+    int k = warp;
+    if (full) {
+      const int16_t* bp = B + (k0 + k) * ldb + col;
+      for (; k + (kGvUnroll - 1) * kGvWarps < kc; k += kGvUnroll * kGvWarps, bp += kGvUnroll * kGvWarps * ldb) {
+        uint4 v[kGvUnroll];
+#pragma unroll
+        for (int u = 0; u < kGvUnroll; ++u) v[u] = __ldg(reinterpret_cast<const uint4*>(bp + u * kGvWarps * ldb));
+#pragma unroll
+        for (int u = 0; u < kGvUnroll; ++u) {
+          const uint32_t xw = xs[k + u * kGvWarps];
+          acc[0] = __viaddmin_s16x2(v[u].x, xw, acc[0]);
+          acc[1] = __viaddmin_s16x2(v[u].y, xw, acc[1]);
+          acc[2] = __viaddmin_s16x2(v[u].z, xw, acc[2]);
+          acc[3] = __viaddmin_s16x2(v[u].w, xw, acc[3]);
+        }
+      }
+    }
+    for (; k < kc && any; k += kGvWarps) {
+      const uint32_t xw = xs[k];
+      const int16_t* bp = B + (k0 + k) * ldb + col;
+      if (full) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(bp));
+        acc[0] = __viaddmin_s16x2(v.x, xw, acc[0]);
+        acc[1] = __viaddmin_s16x2(v.y, xw, acc[1]);
+        acc[2] = __viaddmin_s16x2(v.z, xw, acc[2]);
+        acc[3] = __viaddmin_s16x2(v.w, xw, acc[3]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const uint32_t b = (col + e < N) ? (uint32_t)(uint16_t)bp[e] : (uint32_t)kInf;
+          const uint32_t sh = 16 * (e & 1);
+          const uint32_t cur = (acc[e >> 1] >> sh) & 0xFFFFu;
+          const uint32_t cand = b + (xw & 0xFFFFu);
+          const uint32_t nv = cand < cur ? cand : cur;
+          acc[e >> 1] = (acc[e >> 1] & ~(0xFFFFu << sh)) | (nv << sh);
+        }
+      }
+    }
+  }
+  part[warp][lane] = make_uint4(acc[0], acc[1], acc[2], acc[3]);
+  __syncthreads();
+  if (warp == 0) {
+    uint4 r = part[0][lane];
+    for (int w = 1; w < kGvWarps; ++w) {
+      const uint4 q = part[w][lane];
+      r = make_uint4(__vmins2(r.x, q.x), __vmins2(r.y, q.y), __vmins2(r.z, q.z), __vmins2(r.w, q.w));
+    }
+    part[0][lane] = r;
+  }
+  cluster.sync();  // every CTA's band partial is in its shared memory
+  constexpr int kPerRank = kGvVecs / kGvRanks;
+  if (threadIdx.x < kPerRank) {
+    const int vi = rank * kPerRank + threadIdx.x;
+    uint4 r = make_uint4(kInf2, kInf2, kInf2, kInf2);
+    for (int q = 0; q < kGvRanks; ++q) {
+      const uint4 v = *cluster.map_shared_rank(&part[0][vi], q);
+      r = make_uint4(__vmins2(r.x, v.x), __vmins2(r.y, v.y), __vmins2(r.z, v.z), __vmins2(r.w, v.w));
+    }
+    const int64_t c = (int64_t)blockIdx.x * kGvBand + vi * 8;
+    const uint32_t w4[4] = {r.x, r.y, r.z, r.w};
+    int32_t lm = kInf;
+    if (c + 8 <= N) {
+      *reinterpret_cast<uint4*>(y + c) = r;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) lm = min(lm, (int32_t)((w4[e >> 1] >> (16 * (e & 1))) & 0xFFFF));
+    } else if (c < N) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (c + e < N) {
+          const int32_t v = (int32_t)((w4[e >> 1] >> (16 * (e & 1))) & 0xFFFF);
+          y[c + e] = (int16_t)v;
+          lm = min(lm, v);
+        }
+    }
+    if (min_out != nullptr && lm < kInf) atomicMin(min_out, lm);
+  }
+  cluster.sync();  // no CTA leaves while others may still read its shared memory
+}
+
+// Which GEMV kernel: the cluster one streams long row segments but has N / 256 bands of 8 CTAs;
+// below 16 bands the column-strip kernel keeps more CTAs busy.
+bool gemv_use_clusters(int64_t N) { return N >= 16 * kGvBand; }
+
 extern "C" rd_status rd_minplus_gemv(const int16_t* x, const int16_t* B, int64_t ldb, int16_t* y, int64_t N,
                                      int64_t K, int32_t* min_out, cudaStream_t s) {
   if (N < 0 || K < 0) return RD_ERR_ARG;
@@ -511,10 +626,29 @@ extern "C" rd_status rd_minplus_gemv(const int16_t* x, const int16_t* B, int64_t
     if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
   }
   if (N == 0) return RD_OK;
-  const int64_t grid = (N + kGemvCols - 1) / kGemvCols;
-  if (grid > 0x7FFFFFFF) return RD_ERR_ARG;
-  minplus_gemv_kernel<<<(unsigned)grid, kGemvThreads, 0, s>>>(x, B, ldb, y, N, K, min_out);
-  e = cudaGetLastError();
+  if (gemv_use_clusters(N)) {
+    const int64_t bands = (N + kGvBand - 1) / kGvBand;
+    if (bands > 0x7FFFFFFF) return RD_ERR_ARG;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)bands, kGvRanks, 1);
+    cfg.blockDim = dim3(kGvThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = kGvRanks;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, minplus_gemv_cluster_kernel, x, B, ldb, y, N, K, min_out);
+  } else {
+    const int64_t grid = (N + kGemvCols - 1) / kGemvCols;
+    if (grid > 0x7FFFFFFF) return RD_ERR_ARG;
+    minplus_gemv_kernel<<<(unsigned)grid, kGemvThreads, 0, s>>>(x, B, ldb, y, N, K, min_out);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
   return RD_OK;
 }
