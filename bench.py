@@ -529,6 +529,8 @@ def main() -> None:
     ap.add_argument("--sparse-only", type=int, default=0, metavar="M",
                     help="time only the dense x sparse product A(G) (x) A(G)^2 for m = M (profiler captures)")
     ap.add_argument("--rows-per-block", type=int, default=2, help="R of the sparse form for --sparse-only")
+    ap.add_argument("--gemv-only", type=int, default=0, metavar="N",
+                    help="time only the one-row product against an N x N operand (profiling aid)")
     ap.add_argument("--split-only", type=int, default=0, metavar="M",
                     help="time only the row-split product at m = M (profiling aid)")
     args = ap.parse_args()
@@ -547,6 +549,12 @@ def main() -> None:
         return run_sparse_only(rd, torch, args)
     if args.split_only:
         return run_split_only(rd, torch, args)
+    if args.gemv_only:
+        from paper_2409_17658_gb300 import inputs
+
+        B = inputs.matrix_torch(args.gemv_only, args.gemv_only, seed=SEED_B, device="cuda")
+        print(json.dumps({"gemv_only": args.gemv_only, **gemv_leg(rd, torch, B, args.gemv_only, reps=args.steps)}))
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
