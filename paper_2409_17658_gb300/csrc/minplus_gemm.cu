@@ -54,7 +54,9 @@ __device__ __forceinline__ uint32_t pack2(int16_t lo, int16_t hi) {
 }
 
 // One BM x BN output tile of C = A (x) B at (m0, n0), plus its contribution to the
-// minimum (min_out) and the diagonal minimum (diag_out) when those are not null.
+// minimum (min_out) and the diagonal minimum (diag_out) when those are not null.  SPLIT: the tile
+// of this CTA's K slice is left in shared memory ([BM][BN/2] packed words) for a cluster reduction.
+template <bool SPLIT = false>
 __device__ __forceinline__ void gemm_tile(const int16_t* __restrict__ Ag, const int16_t* __restrict__ Bg,
                                           int16_t* __restrict__ Cg, const int64_t M, const int64_t N,
                                           const int64_t K, const int64_t lda, const int64_t ldb, const int64_t ldc,
@@ -195,6 +197,19 @@ __device__ __forceinline__ void gemm_tile(const int16_t* __restrict__ Ag, const 
     __syncthreads();
   }
 
+  if (SPLIT) {
+    cp_async_wait<0>();
+    __syncthreads();  // no copy in flight and no warp still reading the staging buffers
+    uint4* T = reinterpret_cast<uint4*>(smem);
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int part = 0; part < 2; ++part)
+        T[(ty * 8 + r) * (BN / 8) + part * 16 + tx] =
+            make_uint4(acc[r][part * 4], acc[r][part * 4 + 1], acc[r][part * 4 + 2], acc[r][part * 4 + 3]);
+    return;
+  }
+
   // ---- epilogue: store, and reduce the minimum and the diagonal minimum
   uint32_t vmin = kInf2;
   int32_t dmin = kInf;
@@ -276,6 +291,66 @@ __global__ void __launch_bounds__(NT, 2) minplus_gemm_kernel(GemmParams p) {
   int64_t tm, tn;
   grouped_tile((int64_t)blockIdx.y * gridDim.x + blockIdx.x, gridDim.x, gridDim.y, &tm, &tn);
   gemm_tile(Ag, p.B, Cg, p.M, p.N, p.K, p.lda, p.ldb, p.ldc, tm * BM, tn * BN, p.min_out, p.diag_out, smem);
+}
+
+// ---- split K for small products: a cluster of S CTAs per output tile, CTA r computing the tile over
+// its K slice [r kslice, (r + 1) kslice); the S partial tiles, left in the CTAs' shared memory, meet in
+// distributed shared memory, CTA r min-reducing rows [r BM/S, (r + 1) BM/S) of the tile and writing
+// them (with the minimum).  Used when the output tiles alone would not fill one wave of the GPU.
+__global__ void __launch_bounds__(NT, 2) minplus_gemm_splitk_kernel(GemmParams p, int64_t kslice) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int rank = (int)cluster.block_rank(), S = (int)cluster.num_blocks();
+  int64_t tm, tn;
+  grouped_tile((int64_t)blockIdx.y * gridDim.x + blockIdx.x, gridDim.x, gridDim.y, &tm, &tn);
+  const int64_t m0 = tm * BM, n0 = tn * BN;
+  const int64_t k0 = (int64_t)rank * kslice, k1 = (k0 + kslice < p.K) ? k0 + kslice : p.K;
+  gemm_tile<true>(p.A + k0, p.B + k0 * p.ldb, nullptr, p.M, p.N, k1 - k0, p.lda, p.ldb, p.ldc, m0, n0, nullptr,
+                  nullptr, smem);
+  cluster.sync();  // every partial tile is in place
+  const int rows = BM / S;
+  uint32_t vmin = kInf2;
+  int32_t emin = kInf;
+  for (int v = threadIdx.x; v < rows * (BN / 8); v += NT) {
+    const int row = rank * rows + v / (BN / 8), c8 = v % (BN / 8);
+    uint4 r = make_uint4(kInf2, kInf2, kInf2, kInf2);
+    for (int q = 0; q < S; ++q) {
+      const uint4 t = cluster.map_shared_rank(reinterpret_cast<uint4*>(smem), q)[row * (BN / 8) + c8];
+      r = make_uint4(__vmins2(r.x, t.x), __vmins2(r.y, t.y), __vmins2(r.z, t.z), __vmins2(r.w, t.w));
+    }
+    // the tile's word w covers columns 2w, 2w + 1: vector c8 = part * 16 + tx holds part * 128 + tx * 8 ..
+    const int part = c8 / 16, tx = c8 % 16;
+    const int64_t gi = m0 + row, gj = n0 + part * 128 + tx * 8;
+    if (gi >= p.M || gj >= p.N) continue;
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+    if (gj + 8 <= p.N) {
+      *reinterpret_cast<uint4*>(p.C + gi * p.ldc + gj) = r;
+      vmin = __vmins2(__vmins2(vmin, r.x), __vmins2(__vmins2(r.y, r.z), r.w));
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (gj + e < p.N) {
+          const int32_t x = (int32_t)((w[e >> 1] >> (16 * (e & 1))) & 0xFFFF);
+          p.C[gi * p.ldc + gj + e] = (int16_t)x;
+          emin = min(emin, x);
+        }
+    }
+  }
+  if (p.min_out != nullptr) {
+    int32_t lm = min(emin, min((int32_t)(vmin & 0xFFFF), (int32_t)(vmin >> 16)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lm = min(lm, __shfl_xor_sync(0xFFFFFFFFu, lm, o));
+    __shared__ int32_t red_m[NT / 32];
+    if ((threadIdx.x & 31) == 0) red_m[threadIdx.x >> 5] = lm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int32_t bm = kInf;
+      for (int w2 = 0; w2 < NT / 32; ++w2) bm = min(bm, red_m[w2]);
+      if (bm < kInf) atomicMin(p.min_out, bm);
+    }
+  }
+  cluster.sync();  // no CTA leaves while others may still read its shared memory
 }
 
 // ---- batched products: one persistent launch over the tiles of up to kMaxBatch products
@@ -440,6 +515,9 @@ cudaError_t set_smem_attr() {
     e = cudaFuncSetAttribute(minplus_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
   else if (WHICH == 1)
     e = cudaFuncSetAttribute(minplus_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  else if (WHICH == 3)
+    e = cudaFuncSetAttribute(minplus_gemm_splitk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES);
   else
     e = cudaFuncSetAttribute(minplus_gemm_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)SMEM_BYTES);
@@ -454,12 +532,48 @@ cudaError_t launch_fill_i32(int32_t* dst, int32_t value, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Split K when the output tiles alone fill less than one wave (2 CTAs per SM): S in {2, 4, 8}, the
+// smallest that fills it, with every K slice at least 4 k-tiles deep and none empty.
+int splitk_factor(int64_t tiles, int64_t K) {
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t wave = 2 * (int64_t)sms;
+  int S = 1;
+  while (S < 8 && tiles * S < wave && K >= (int64_t)(2 * S) * 4 * BK) S *= 2;
+  if (S > 1) {
+    const int64_t kslice = ((K + S - 1) / S + BK - 1) / BK * BK;
+    while (S > 1 && (int64_t)(S - 1) * kslice >= K) S /= 2;  // every slice non-empty
+  }
+  return S;
+}
+
 cudaError_t launch_minplus_gemm(const GemmParams& p, bool ring, cudaStream_t s) {
   const int64_t gx = (p.N + BN - 1) / BN, gy = (p.M + BM - 1) / BM;
   if (gx <= 0 || gy <= 0) return cudaSuccess;
   if (gx > 0x7FFFFFFF || gy > 65535) return cudaErrorInvalidConfiguration;
   const dim3 grid((unsigned)gx, (unsigned)gy);
   cudaError_t e;
+  const int S = (ring || p.diag_out != nullptr) ? 1 : splitk_factor(gx * gy, p.K);  // no diagonal in the split form
+  if (S > 1) {
+    e = set_smem_attr<3>();
+    if (e != cudaSuccess) return e;
+    const int64_t kslice = ((p.K + S - 1) / S + BK - 1) / BK * BK;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)gx, (unsigned)gy, (unsigned)S);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = (unsigned)S;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, minplus_gemm_splitk_kernel, p, kslice);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
   if (ring) {
     e = set_smem_attr<1>();
     if (e != cudaSuccess) return e;

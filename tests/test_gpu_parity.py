@@ -87,7 +87,9 @@ def test_transfer_matrix_m9_rows(rd, orc):
 # ---------------------------------------------------------------- a3: (min,+) GEMM
 
 SHAPES = [(1, 1, 1), (7, 9, 5), (33, 33, 33), (128, 256, 32), (129, 257, 33), (300, 520, 700), (1, 777, 640),
-          (640, 8, 1000), (1000, 1000, 1000)]
+          (640, 8, 1000), (1000, 1000, 1000),
+          # few output tiles and a long K: the split-K cluster form (8 and 4 slices, ragged last slice)
+          (257, 300, 1500), (130, 260, 1030)]
 
 
 @pytest.mark.parametrize("dist", ["u32", "wide", "dense"])
