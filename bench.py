@@ -169,6 +169,14 @@ def time_to_period(rd, torch, ms: list[int], with_oracle: bool) -> dict:
         # one untimed pass (first touch of allocations, module load), then the timed one; N <= 128 runs
         # the single-CTA search of rd_power_until_periodic (no plan), larger N the row-split step
         small = n <= 128
+        tuned = None
+        if not small:
+            # the native autotuner picks the passes' launch shape (outside the timed region); the plan
+            # built inside the timed region then takes it from the library's tuning table
+            tplan = rd.split_plan(m, x_ld=ld)
+            T = torch.empty_like(A)
+            tuned = rd.tune_split(tplan, A, T, reps=2)
+            del tplan, T
         for _ in range(2):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -199,7 +207,7 @@ def time_to_period(rd, torch, ms: list[int], with_oracle: bool) -> dict:
         entry = {"N": n, "nnz_A": nnz, "k": r["k"], "p": r["p"], "q": r["q"], "products": products, "gpu_s": dt,
                  "step": ("single-CTA search (N <= 128)" if small else
                           f"row split j={info.j} (w {info.w1}/{info.w2}, slabs per CTA {info.k1}/{info.k2})"),
-                 "us_per_power": dt / r["j"] * 1e6,
+                 "us_per_power": dt / r["j"] * 1e6, "tuned_shape": tuned,
                  "split_product_ms": prod_ms, "split_x_rows": info.x_rows,
                  "split_product_GBps": moved / (prod_ms * 1e-3) / 1e9,
                  "split_product_frac_of_measured_hbm": moved / (prod_ms * 1e-3) / 1e9 / HBM_GBS,
@@ -319,6 +327,7 @@ def run_split_only(rd, torch, args) -> None:
     C = torch.empty_like(A)
     plan = rd.split_plan(m, x_ld=A.stride(0))
     rd.split_minplus(plan, A, P)  # P = A (x) A, dense enough to stand for a power
+    tuned = rd.tune_split(plan, P, C, reps=2) if args.tune else None
     for _ in range(args.warmup):
         rd.split_minplus(plan, P, C)
     torch.cuda.synchronize()
@@ -331,7 +340,8 @@ def run_split_only(rd, torch, args) -> None:
     ms = float(np.mean([s0.elapsed_time(s1) for s0, s1 in evs]))
     info = plan["info"]
     moved = (2 * n + 2 * info.x_rows) * n * 2
-    print(json.dumps({"split_only_m": m, "N": n, "plan": info.as_dict(), "ms": ms, "bytes_per_product": moved,
+    print(json.dumps({"split_only_m": m, "N": n, "plan": info.as_dict(), "tuned": tuned, "ms": ms,
+                      "bytes_per_product": moved,
                       "GBps": moved / (ms * 1e-3) / 1e9, "frac_of_measured_hbm": moved / (ms * 1e-3) / 1e9 / HBM_GBS}))
 
 
@@ -355,6 +365,36 @@ def gemv_leg(rd, torch, B, n: int, reps: int = 20) -> dict:
     return {"N": n, "ms": ms, "GB_per_s": nbytes / (ms * 1e-3) / 1e9, "bound": "hbm",
             "frac_of_measured_hbm": nbytes / (ms * 1e-3) / 1e9 / HBM_GBS, "addmin_gops": float(n) * n / (ms * 1e-3) / 1e9,
             "l2": "B is 512 MiB > L2; consecutive calls re-read it from HBM"}
+
+
+def gemm_sweep(rd, torch, sizes=(1024, 2048, 4096, 32768)) -> dict:
+    """The dense product at the sweep's other sizes (the headline size is the main line): the native
+    autotuner picks the split-K factor per size class (outside the timed region), then CUDA events time
+    the product as a caller launches it."""
+    from paper_2409_17658_gb300 import inputs
+
+    out = {}
+    for n in sizes:
+        A = inputs.matrix_torch(n, n, seed=SEED_A, device="cuda")
+        B = inputs.matrix_torch(n, n, seed=SEED_B, device="cuda")
+        C = torch.empty((n, n), dtype=torch.int16, device="cuda")
+        reps = 2 if n > 16384 else 10
+        tuned = rd.tune_gemm(A, B, C, reps=1 if n > 16384 else 3)
+        rd.minplus_gemm(A, B, C)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            rd.minplus_gemm(A, B, C)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        gops = float(n) ** 3 / (ms * 1e-3) / 1e9
+        out[f"N={n}"] = {"ms": ms, "gops": gops, "frac_of_peak": gops / PEAK_GOPS, "split_k": tuned["p"][0],
+                         "tuner_ms": tuned["ms"]}
+        del A, B, C
+        torch.cuda.empty_cache()
+    return out
 
 
 def batched_products(rd, torch, count: int = 64, seed: int = 4) -> dict:
@@ -533,6 +573,10 @@ def main() -> None:
                     help="time only the one-row product against an N x N operand (profiling aid)")
     ap.add_argument("--split-only", type=int, default=0, metavar="M",
                     help="time only the row-split product at m = M (profiling aid)")
+    ap.add_argument("--tune", action="store_true", help="with --split-only: run the autotuner on the plan first")
+    ap.add_argument("--tune-table", default="", metavar="PATH",
+                    help="load a saved tuning table (JSON, paper_2409_17658_gb300.tuning) before running")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the dense sweep at the other sizes")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -545,6 +589,10 @@ def main() -> None:
 
     build.build()
     torch.cuda.set_device(local)
+    if args.tune_table:
+        from paper_2409_17658_gb300 import tuning
+
+        tuning.load(args.tune_table)
     if args.sparse_only:
         return run_sparse_only(rd, torch, args)
     if args.split_only:
@@ -652,13 +700,17 @@ def main() -> None:
     extra = {}
     if rank == 0:
         extra["gemv"] = gemv_leg(rd, torch, B, n)
-    if rank == 0 and not args.no_serving:
-        extra["serving"] = serving(rd)
-    if rank == 0 and not args.no_batched:
-        extra["batched"] = batched_products(rd, torch)
+    if rank == 0 and not args.no_sweep:
+        extra["gemm_sweep"] = gemm_sweep(rd, torch)
     if rank == 0 and not args.no_period:
         extra["time_to_period"] = time_to_period(rd, torch, [3, 7, 9, 10], with_oracle=not args.no_cpu)
         extra["small_case"] = small_case(rd, torch)
+    if rank == 0 and not args.no_serving:
+        extra["serving"] = serving(rd)  # its row-split plans take the shapes tuned above
+    if rank == 0 and not args.no_batched:
+        extra["batched"] = batched_products(rd, torch)
+    if rank == 0:
+        extra["tuning_table"] = rd.tune_table()
     if rank == 0 and not args.no_cpu:
         extra["cpu_baseline"] = cpu_baseline_gemm(a, b, rows=32)
 

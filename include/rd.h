@@ -262,8 +262,9 @@ rd_status rd_power_until_periodic_sparse(const int16_t *A_dev, int64_t N, int64_
  * power step) with CUDA events, and returns the fastest R in *best_R;
  * ms_per_R[0..3] (nullable) receives the times (-1 for a candidate whose plan
  * did not fit).  scratch_dev (256-byte aligned) must hold an N x lda int16
- * result plus the plans; a power work buffer's ring is large enough.
- * Synchronous.
+ * result plus the plans; a power work buffer's ring is large enough.  The
+ * fastest R is also recorded as the RD_TUNE_SPARSE_R entry for N's size class
+ * in the tuning table (below).  Synchronous.
  */
 rd_status rd_sparse_tune(const int16_t *A, int64_t lda, int64_t N, void *scratch_dev, size_t scratch_bytes,
                          int *best_R, float *ms_per_R, cudaStream_t s);
@@ -304,6 +305,8 @@ rd_status rd_sparse_tune(const int16_t *A, int64_t lda, int64_t N, void *scratch
  *   lmax1, lmax2    list entries of one fiber at most (staged with it);
  *   k1, k2   column slabs one CTA sweeps per fiber (1..64, default 8; a
  *            caller may change them like w1, w2);
+ *            an RD_TUNE_SPLIT entry of the tuning table for (m, j) replaces
+ *            the defaults of w1, k1, w2, k2 when its widths fit;
  *   chunk_cols  0 (default): both passes run over all N columns, X has
  *            x_rows x N entries; > 0 (a multiple of 128): they run chunk by
  *            chunk of that many columns and X holds one chunk (x_rows x
@@ -479,10 +482,84 @@ rd_status rd_power_until_periodic_noalloc(const int16_t *A_dev, int64_t N, int64
                                           cudaStream_t s);
 
 /*
+ * Tuning table and autotuners.  The launch shape of three kernels is a choice
+ * that changes time, never results: the split-K factor S of rd_minplus_gemm
+ * (mode RD_TUNE_GEMM_SPLITK), the slab widths and slabs per CTA of the
+ * row-split passes (RD_TUNE_SPLIT) and the rows per block of the sparse step
+ * (RD_TUNE_SPARSE_R).  The library keeps one process-wide table of entries
+ * keyed by (mode, key, aux):
+ *   RD_TUNE_GEMM_SPLITK  key = rd_tune_bucket(max(M, N)), aux =
+ *                        rd_tune_bucket(K); p[0] = S in {1, 2, 4, 8};
+ *   RD_TUNE_SPLIT        key = m, aux = j; p[0..3] = w1, k1, w2, k2 (widths
+ *                        32, 64 or 128; slabs per CTA 1..64);
+ *   RD_TUNE_SPARSE_R     key = rd_tune_bucket(N), aux = 0; p[0] = R in
+ *                        {1, 2, 4, 8};
+ * ms is the time the autotuner measured for the entry (informational).
+ * rd_minplus_gemm takes S from a matching entry (when S suits the product:
+ * every K slice non-empty; else its built-in rule), rd_split_plan takes the
+ * widths and slabs per CTA from a matching entry (when the plan's staged rows
+ * fit with them; else its built-in choice).  RD_TUNE_SPARSE_R entries are
+ * recorded for the caller, who passes R to the sparse calls.  The autotuners
+ * time their candidates with CUDA events and record the fastest; the table is
+ * read and written as a whole by rd_tune_get / rd_tune_set, so a caller can
+ * keep it in a file.  Thread-safe (one mutex); host-only except the timed
+ * launches of the autotuners.
+ */
+enum { RD_TUNE_GEMM_SPLITK = 1, RD_TUNE_SPLIT = 2, RD_TUNE_SPARSE_R = 3 };
+#define RD_TUNE_MAX 256 /* entries the table holds */
+typedef struct {
+  int32_t mode, key, aux;
+  int32_t p[4];
+  float ms;
+} rd_tune_entry_t;
+
+/* rd_tune_bucket -- ceil(log2(x)) for x >= 1 (0 for x <= 1): the size class
+ * the table keys use. */
+int rd_tune_bucket(int64_t x);
+
+/* rd_tune_set -- replaces the table by entries[0..count) (count 0 clears it).
+ * RD_ERR_ARG (table unchanged) when count is outside [0, RD_TUNE_MAX], entries
+ * is null with count > 0, an entry has an unknown mode or parameters outside
+ * the ranges above, or two entries share (mode, key, aux). */
+rd_status rd_tune_set(const rd_tune_entry_t *entries, int count);
+
+/* rd_tune_get -- copies up to cap entries into entries (nullable when cap is
+ * 0) and sets *count to the number the table holds. */
+rd_status rd_tune_get(rd_tune_entry_t *entries, int cap, int *count);
+
+/* rd_tune_lookup -- the entry for (mode, key, aux) into *out; RD_NOT_FOUND
+ * when there is none. */
+rd_status rd_tune_lookup(int mode, int key, int aux, rd_tune_entry_t *out);
+
+/*
+ * rd_tune_gemm -- autotuner for the split-K factor of rd_minplus_gemm on an
+ * M x N x K product (operands as in rd_minplus_gemm, M >= 2; C is
+ * overwritten): times each S in {1, 2, 4, 8} that suits the product and
+ * would not exceed four waves of CTAs (one warm-up, then reps >= 1 timed
+ * products), records the fastest in the table (replacing an entry with the
+ * same key) and returns it in *best (nullable).  Synchronous.
+ */
+rd_status rd_tune_gemm(const int16_t *A, int64_t lda, const int16_t *B, int64_t ldb, int16_t *C, int64_t ldc,
+                       int64_t M, int64_t N, int64_t K, int reps, rd_tune_entry_t *best, cudaStream_t s);
+
+/*
+ * rd_tune_split -- autotuner for the launch shape of the row-split passes of
+ * a built plan (arguments as in rd_split_minplus; X and C are overwritten):
+ * times rd_split_minplus over the widths {32, 64, 128} that fit and slabs per
+ * CTA {1, 2, 4, 8, 16, 32}, first for pass 1 with pass 2 as in *info, then
+ * for pass 2 with pass 1 at its best (one warm-up and reps >= 1 timed
+ * products per candidate).  Writes the best w1, k1, w2, k2 into *info,
+ * records them in the table under (m, j) and returns the entry in *best
+ * (nullable).  Synchronous.
+ */
+rd_status rd_tune_split(rd_split_info_t *info, const void *plan_dev, const int16_t *B, int64_t ldb, int16_t *X_dev,
+                        int64_t ldx, int16_t *C, int64_t ldc, int reps, rd_tune_entry_t *best, cudaStream_t s);
+
+/*
  * rd_gamma_R -- gamma_R(P_m box C_n) for m in [1, RD_MAX_M], n >= 3 (C_n needs
- * n >= 3).  The first call for a given m builds A(G) and runs
- * rd_power_until_periodic_split (m >= 2; m = 1 uses
- * rd_power_until_periodic_sparse) on the current device, in device memory this
+ * n >= 3).  The first call for a given m builds A(G) and runs the period
+ * search: in one CTA (rd_power_until_periodic) when C_m <= 128 (m <= 4), else
+ * by rd_power_until_periodic_split, on the current device, in device memory this
  * call allocates and frees (about 11 powers of C_m x C_m int16: 10 GB at m = 9,
  * 87 GB at m = 10; RD_ERR_NOMEM when that does not fit); the result (gamma for n < k + p, and (k, p, q)) is
  * cached per m for the life of the process, and later calls evaluate the

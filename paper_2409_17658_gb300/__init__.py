@@ -84,6 +84,15 @@ def _lib():
         lib.rd_split_minplus.argtypes = [vp, vp, vp, i64, vp, i64, vp, i64, vp, vp]
         lib.rd_power_until_periodic_split.argtypes = [vp, i64, vp, vp, vp, i64, ctypes.c_int, vp, sz, vp, vp, vp,
                                                       vp, vp]
+        lib.rd_tune_bucket.argtypes = [i64]
+        lib.rd_tune_bucket.restype = ctypes.c_int
+        lib.rd_tune_set.argtypes = [vp, ctypes.c_int]
+        lib.rd_tune_get.argtypes = [vp, ctypes.c_int, vp]
+        lib.rd_tune_lookup.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
+        lib.rd_tune_gemm.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, ctypes.c_int, vp, vp]
+        lib.rd_tune_split.argtypes = [vp, vp, vp, i64, vp, i64, vp, i64, ctypes.c_int, vp, vp]
+        for name in ("rd_tune_set", "rd_tune_get", "rd_tune_lookup", "rd_tune_gemm", "rd_tune_split"):
+            getattr(lib, name).restype = st
         for name in ("rd_state_count", "rd_padded_dim", "rd_enumerate_states", "rd_build_transfer",
                      "rd_minplus_gemm", "rd_power_work_bytes", "rd_power_until_periodic", "rd_gamma_R",
                      "rd_power_slot", "rd_power_until_periodic_noalloc", "rd_sparse_count", "rd_sparse_build",
@@ -459,6 +468,77 @@ def power_until_periodic_split(A, plan: dict, kmax: int, work, stream=None) -> d
     j = k.value + p.value if found else kmax
     return dict(status=st, found=found, k=k.value if found else None, p=p.value if found else None,
                 q=q.value if found else None, j=j, gamma=gamma)
+
+
+# ---------------------------------------------------------------- tuning table and autotuners
+
+RD_TUNE_GEMM_SPLITK, RD_TUNE_SPLIT, RD_TUNE_SPARSE_R = 1, 2, 3
+RD_TUNE_MAX = 256
+TUNE_MODES = {RD_TUNE_GEMM_SPLITK: "gemm_splitk", RD_TUNE_SPLIT: "split", RD_TUNE_SPARSE_R: "sparse_r"}
+
+
+class TuneEntry(ctypes.Structure):
+    """rd_tune_entry_t of include/rd.h."""
+    _fields_ = [("mode", ctypes.c_int32), ("key", ctypes.c_int32), ("aux", ctypes.c_int32),
+                ("p", ctypes.c_int32 * 4), ("ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return dict(mode=TUNE_MODES.get(self.mode, self.mode), key=self.key, aux=self.aux, p=list(self.p),
+                    ms=round(float(self.ms), 6))
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "TuneEntry":
+        names = {v: k for k, v in TUNE_MODES.items()}
+        mode = names.get(d["mode"], d["mode"])
+        p = list(d["p"]) + [0] * (4 - len(d["p"]))
+        return cls(int(mode), int(d["key"]), int(d["aux"]), (ctypes.c_int32 * 4)(*p[:4]), float(d.get("ms", -1.0)))
+
+
+def tune_bucket(x: int) -> int:
+    """ceil(log2(x)): the size class of the tuning table's keys."""
+    return _lib().rd_tune_bucket(int(x))
+
+
+def tune_table() -> list[dict]:
+    """The library's tuning table, one dict per entry."""
+    n = ctypes.c_int()
+    arr = (TuneEntry * RD_TUNE_MAX)()
+    _check(_lib().rd_tune_get(arr, RD_TUNE_MAX, ctypes.byref(n)), "rd_tune_get")
+    return [arr[i].as_dict() for i in range(n.value)]
+
+
+def tune_set(entries: list[dict]) -> None:
+    """Replace the library's tuning table (an empty list clears it)."""
+    arr = (TuneEntry * max(1, len(entries)))(*[TuneEntry.from_dict(e) for e in entries])
+    _check(_lib().rd_tune_set(arr, len(entries)), "rd_tune_set")
+
+
+def tune_lookup(mode: int, key: int, aux: int) -> dict | None:
+    out = TuneEntry()
+    st = _check(_lib().rd_tune_lookup(mode, key, aux, ctypes.byref(out)), "rd_tune_lookup", ok=(RD_OK, RD_NOT_FOUND))
+    return out.as_dict() if st == RD_OK else None
+
+
+def tune_gemm(A, B, C, M: int | None = None, N: int | None = None, K: int | None = None, reps: int = 3,
+              stream=None) -> dict:
+    """Native autotuner of the split-K factor of minplus_gemm for an M x N x K product (C is overwritten)."""
+    M = C.shape[0] if M is None else M
+    N = C.shape[1] if N is None else N
+    K = A.shape[1] if K is None else K
+    out = TuneEntry()
+    _check(_lib().rd_tune_gemm(_dptr(A), A.stride(0), _dptr(B), B.stride(0), _dptr(C), C.stride(0), M, N, K, reps,
+                               ctypes.byref(out), _stream(stream)), "rd_tune_gemm")
+    return out.as_dict()
+
+
+def tune_split(plan: dict, B, C, reps: int = 2, stream=None) -> dict:
+    """Native autotuner of the row-split passes' launch shape; updates plan["info"] (X and C are overwritten)."""
+    out = TuneEntry()
+    X = plan["X"]
+    _check(_lib().rd_tune_split(ctypes.byref(plan["info"]), _dptr(plan["plan"]), _dptr(B), B.stride(0), _dptr(X),
+                                X.stride(0), _dptr(C), C.stride(0), reps, ctypes.byref(out), _stream(stream)),
+           "rd_tune_split")
+    return out.as_dict()
 
 
 def power_slot(n: int, ld: int, kmax: int, work_bytes: int, k: int) -> int:

@@ -547,13 +547,33 @@ int splitk_factor(int64_t tiles, int64_t K) {
   return S;
 }
 
-cudaError_t launch_minplus_gemm(const GemmParams& p, bool ring, cudaStream_t s) {
+bool splitk_suits(int S, int64_t K) {
+  if (S == 1) return true;
+  if (S != 2 && S != 4 && S != 8) return false;
+  const int64_t kslice = ((K + S - 1) / S + BK - 1) / BK * BK;
+  return (int64_t)(S - 1) * kslice < K;
+}
+
+int64_t gemm_tiles(int64_t M, int64_t N) { return ((M + BM - 1) / BM) * ((N + BN - 1) / BN); }
+
+cudaError_t launch_minplus_gemm(const GemmParams& p, bool ring, cudaStream_t s, int force_splitk) {
   const int64_t gx = (p.N + BN - 1) / BN, gy = (p.M + BM - 1) / BM;
   if (gx <= 0 || gy <= 0) return cudaSuccess;
   if (gx > 0x7FFFFFFF || gy > 65535) return cudaErrorInvalidConfiguration;
   const dim3 grid((unsigned)gx, (unsigned)gy);
   cudaError_t e;
-  const int S = (ring || p.diag_out != nullptr) ? 1 : splitk_factor(gx * gy, p.K);  // no diagonal in the split form
+  int S = 1;  // ring mode and the diagonal output keep one CTA per tile (no diagonal in the split form)
+  if (force_splitk > 0) {
+    if (ring || p.diag_out != nullptr || !splitk_suits(force_splitk, p.K)) return cudaErrorInvalidValue;
+    S = force_splitk;
+  } else if (!ring && p.diag_out == nullptr) {
+    rd_tune_entry_t t;
+    const int64_t mn = p.M > p.N ? p.M : p.N;
+    if (tune_find(RD_TUNE_GEMM_SPLITK, rd_tune_bucket(mn), rd_tune_bucket(p.K), &t) && splitk_suits(t.p[0], p.K))
+      S = t.p[0];
+    else
+      S = splitk_factor(gx * gy, p.K);
+  }
   if (S > 1) {
     e = set_smem_attr<3>();
     if (e != cudaSuccess) return e;

@@ -79,7 +79,18 @@ struct GemmParams {
 };
 
 // Launchers implemented in the .cu files.
-cudaError_t launch_minplus_gemm(const GemmParams& p, bool ring, cudaStream_t s);
+// force_splitk > 0 (not in ring mode): split K by exactly that factor (the autotuner's trials); else the
+// tuning table's factor for the product's size class, else the built-in rule.
+cudaError_t launch_minplus_gemm(const GemmParams& p, bool ring, cudaStream_t s, int force_splitk = 0);
+bool splitk_suits(int S, int64_t K);         // S in {1, 2, 4, 8} and every K slice non-empty
+int64_t gemm_tiles(int64_t M, int64_t N);  // output tiles (CTAs of an unsplit launch)
+
+// The tuning table (tune.cu): lookup and insert-or-replace by (mode, key, aux).
+bool tune_find(int mode, int key, int aux, rd_tune_entry_t* out);
+bool tune_put(const rd_tune_entry_t& e);
+
+// Row-split passes (split.cu): whether slab width W fits with max_slots staged rows.
+bool split_width_fits(int W, int max_slots);
 cudaError_t launch_fill_i32(int32_t* dst, int32_t value, cudaStream_t s);
 
 // One run of the period search (power.cu): the device state, the ring of powers and the operand.

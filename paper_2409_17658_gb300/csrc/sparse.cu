@@ -423,5 +423,11 @@ extern "C" rd_status rd_sparse_tune(const int16_t* A, int64_t lda, int64_t N, vo
   if (rc != RD_OK) return rc;
   if (best == 0) return RD_ERR_NOMEM;
   *best_R = best;
+  rd_tune_entry_t t{};
+  t.mode = RD_TUNE_SPARSE_R;
+  t.key = rd_tune_bucket(N);
+  t.p[0] = best;
+  t.ms = best_ms;
+  tune_put(t);  // a full table keeps its entries; the caller still has *best_R
   return RD_OK;
 }

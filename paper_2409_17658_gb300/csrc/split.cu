@@ -1041,6 +1041,9 @@ cudaError_t read_i32(const int32_t* dev, int32_t* host, int n, cudaStream_t s) {
 }
 
 }  // namespace
+
+bool split_width_fits(int W, int max_slots) { return valid_w(W, max_slots); }
+
 }  // namespace rd
 
 using namespace rd;
@@ -1209,6 +1212,13 @@ extern "C" rd_status rd_split_plan(int m, int j, void* plan_dev, size_t plan_byt
   info->k1 = kDefaultSlabsPerCta;
   info->k2 = kDefaultSlabsPerCta;
   info->chunk_cols = 0;
+  rd_tune_entry_t t;  // a tuned launch shape for this (m, j), when its widths fit this plan
+  if (tune_find(RD_TUNE_SPLIT, m, j, &t) && valid_w(t.p[0], slots1) && valid_w(t.p[2], slots2)) {
+    info->w1 = t.p[0];
+    info->k1 = t.p[1];
+    info->w2 = t.p[2];
+    info->k2 = t.p[3];
+  }
   return RD_OK;
 }
 
