@@ -522,6 +522,15 @@ struct SplitPass {
 
 __device__ __forceinline__ uint32_t min3(uint32_t a, uint32_t b, uint32_t c) { return __vimin3_s16x2(a, b, c); }
 
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <int SET>
 __device__ __forceinline__ void fold_pair(uint4 (&acc)[4], const uint4& v0, const uint4& v1) {
 #pragma unroll
@@ -575,7 +584,7 @@ __host__ __device__ inline PassSmem pass_smem_layout(int max_slots, int n_groups
 }
 
 template <int W, bool FIRST, bool RING, bool STAGED>
-__global__ void __launch_bounds__(kSplitThreads) split_pass_kernel(SplitPass a) {
+__global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 3) split_pass_kernel(SplitPass a) {
   extern __shared__ uint4 sm[];
   constexpr int LR = W / 8;              // threads per row of the slab
   constexpr int G = kSplitThreads / LR;  // groups (resp. staged rows) handled side by side
@@ -641,44 +650,32 @@ __global__ void __launch_bounds__(kSplitThreads) split_pass_kernel(SplitPass a) 
     const int64_t c = sb * W + lane * 8;
     const bool ok = c < a.ncols;
     __syncthreads();  // the metadata is staged / the previous slab has been consumed
-    for (int s0 = gi; s0 < nst; s0 += 4 * G) {
-      int32_t e[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int s = s0 + u * G;
-        e[u] = -1;
-        if (s >= 1 && s < nst) {
-          if (FIRST)
-            e[u] = STAGED ? smem_words[s - 1] : __ldg(a.fmem + f0 + s - 1);
-          else
-            e[u] = f0 + s - 1;
+    // every row segment of the slab goes in flight at once (asynchronous 16-byte copies, no registers)
+#pragma unroll 1
+    for (int s = gi; s < nst; s += G) {
+      const int32_t e = (s < 1) ? -1 : FIRST ? (STAGED ? smem_words[s - 1] : __ldg(a.fmem + f0 + s - 1)) : f0 + s - 1;
+      if (ok && e >= 0)
+        cp_async16(&sm[s * LR + lane], in + (int64_t)(FIRST ? (e >> 5) : e) * a.ldin + c);
+      else
+        sm[s * LR + lane] = inf4;
+    }
+    cp_async_wait_all();
+    if (FIRST && ok) {
+      // pass 1 stages w(p) + B[p]: each thread adds the weights to the vectors it copied itself
+#pragma unroll 1
+      for (int s = gi + (gi < 1 ? G : 0); s < nst; s += G) {
+        const int32_t e = STAGED ? smem_words[s - 1] : __ldg(a.fmem + f0 + s - 1);
+        const uint4 x = sm[s * LR + lane];
+        const uint32_t w2 = (uint32_t)(e & 31) * 0x00010001u;
+        const uint4 v = make_uint4(__viaddmin_s16x2(x.x, w2, kInf2), __viaddmin_s16x2(x.y, w2, kInf2),
+                                   __viaddmin_s16x2(x.z, w2, kInf2), __viaddmin_s16x2(x.w, w2, kInf2));
+        sm[s * LR + lane] = v;
+        if (RING && a.norm) {
+          // min of A(G) (x) P = min over p, x of w(p) + P[p][x] (every word has a predecessor)
+          uint32_t t[4] = {v.x, v.y, v.z, v.w};
+          if (c + 8 > a.ncols) mask_tail(t, (int)(a.ncols - c));  // lanes past the chunk / N
+          mv = min3(min3(mv, t[0], t[1]), min3(t[2], t[3], kInf2), kInf2);
         }
-      }
-      uint4 v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        v[u] = inf4;
-        if (ok && e[u] >= 0) {
-          if (FIRST) {
-            const uint4 x = __ldg(reinterpret_cast<const uint4*>(in + (int64_t)(e[u] >> 5) * a.ldin + c));
-            const uint32_t w2 = (uint32_t)(e[u] & 31) * 0x00010001u;
-            v[u] = make_uint4(__viaddmin_s16x2(x.x, w2, kInf2), __viaddmin_s16x2(x.y, w2, kInf2),
-                              __viaddmin_s16x2(x.z, w2, kInf2), __viaddmin_s16x2(x.w, w2, kInf2));
-            if (RING && a.norm) {
-              // min of A(G) (x) P = min over p, x of w(p) + P[p][x] (every word has a predecessor)
-              uint32_t t[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-              if (c + 8 > a.ncols) mask_tail(t, (int)(a.ncols - c));  // lanes past the chunk / N
-              mv = min3(min3(mv, t[0], t[1]), min3(t[2], t[3], kInf2), kInf2);
-            }
-          } else {
-            v[u] = __ldg(reinterpret_cast<const uint4*>(in + (int64_t)e[u] * a.ldin + c));
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int s = s0 + u * G;
-        if (s < nst) sm[s * LR + lane] = v[u];
       }
     }
     __syncthreads();
