@@ -571,20 +571,20 @@ __device__ __forceinline__ void fold_sublist(uint4 (&acc)[4], const uint4* sm, c
 struct PassSmem {
   size_t gls, go, lst, mem, ord, bytes;
 };
-__host__ __device__ inline PassSmem pass_smem_layout(int max_slots, int n_groups, int max_list, int W) {
+__host__ __device__ inline PassSmem pass_smem_layout(int max_slots, int n_groups, int max_list, int W, bool words) {
   PassSmem p;
   const size_t data = (size_t)(max_slots + 1) * (size_t)W * 2;
   p.gls = data;
   p.go = p.gls + (size_t)n_groups * kRec * 2;
   p.lst = p.go + (size_t)n_groups * 4 * 4;
   p.mem = p.lst + ((size_t)max_list * 2 + 15) / 16 * 16;
-  p.ord = p.mem + ((size_t)max_slots * 4 + 15) / 16 * 16;
+  p.ord = p.mem + (words ? ((size_t)max_slots * 4 + 15) / 16 * 16 : 0);  // words: pass 1 only
   p.bytes = p.ord + ((size_t)n_groups * 2 + 15) / 16 * 16;
   return p;
 }
 
 template <int W, bool FIRST, bool RING, bool STAGED>
-__global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 3) split_pass_kernel(SplitPass a) {
+__global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 4) split_pass_kernel(SplitPass a) {
   extern __shared__ uint4 sm[];
   constexpr int LR = W / 8;              // threads per row of the slab
   constexpr int G = kSplitThreads / LR;  // groups (resp. staged rows) handled side by side
@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 3) split_pass_kerne
   // stage the fiber's metadata once: sub-list bounds relative to the fiber's first list entry,
   // output rows, the list itself (its bounds are even, so it moves as 32-bit pairs) and, in pass 1,
   // the words of the fiber
-  const PassSmem lay = pass_smem_layout(a.max_slots, a.n_groups, a.max_list, W);
+  const PassSmem lay = pass_smem_layout(a.max_slots, a.n_groups, a.max_list, W, FIRST);
   char* smb = reinterpret_cast<char*>(sm);
   uint16_t* sgls = reinterpret_cast<uint16_t*>(smb + lay.gls);
   int4* sgo = reinterpret_cast<int4*>(smb + lay.go);
@@ -815,8 +815,8 @@ constexpr size_t kSmemLimit = 220 * 1024;
 // Staging needs the fiber's list positions to fit the uint16 offsets.
 bool stageable(int max_list, size_t bytes, size_t limit) { return max_list <= 0xFFFF && bytes <= limit; }
 
-size_t pass_smem(int max_slots, int n_groups, int max_list, int W, bool* staged) {
-  const size_t full = pass_smem_layout(max_slots, n_groups, max_list, W).bytes;
+size_t pass_smem(int max_slots, int n_groups, int max_list, int W, bool words, bool* staged) {
+  const size_t full = pass_smem_layout(max_slots, n_groups, max_list, W, words).bytes;
   *staged = stageable(max_list, full, kSmemLimit);
   return *staged ? full : (size_t)(max_slots + 1) * (size_t)W * 2;
 }
@@ -824,12 +824,12 @@ size_t pass_smem(int max_slots, int n_groups, int max_list, int W, bool* staged)
 // Slab width: 128 or 64 columns when the staged fiber leaves room for 3 CTAs per SM (narrower slabs
 // put more groups in a warp and cost shared-memory bank conflicts), else the widest that fits 2 or
 // 1; then the same for the rows alone.
-int choose_w(int max_slots, int n_groups, int max_list) {
+int choose_w(int max_slots, int n_groups, int max_list, bool words) {
   const int ws[3] = {128, 64, 32};
   const size_t limits[3] = {72 * 1024, 112 * 1024, kSmemLimit};
   for (size_t lim : limits)
     for (int w : ws)
-      if (stageable(max_list, pass_smem_layout(max_slots, n_groups, max_list, w).bytes, lim)) return w;
+      if (stageable(max_list, pass_smem_layout(max_slots, n_groups, max_list, w, words).bytes, lim)) return w;
   for (size_t lim : limits)
     for (int w : ws)
       if ((size_t)(max_slots + 1) * (size_t)w * 2 <= lim) return w;
@@ -875,7 +875,7 @@ cudaError_t ensure_limits() {
 template <bool FIRST, bool RING>
 cudaError_t launch_pass(const SplitPass& a, int W, int64_t fibers, cudaStream_t s) {
   bool staged = false;
-  const size_t smem = pass_smem(a.max_slots, a.n_groups, a.max_list, W, &staged);
+  const size_t smem = pass_smem(a.max_slots, a.n_groups, a.max_list, W, FIRST, &staged);
   const int64_t slabs = (a.ncols + W - 1) / W;
   const dim3 grid((unsigned)((slabs + a.slabs_per_cta - 1) / a.slabs_per_cta), (unsigned)fibers);
   void (*k)(SplitPass) = nullptr;
@@ -1175,7 +1175,7 @@ extern "C" rd_status rd_split_plan(int m, int j, void* plan_dev, size_t plan_byt
   e = cudaGetLastError();
   if (e == cudaSuccess) e = read_i32(counters + 2, lm, 2, s);
   if (e != cudaSuccess) return fail(e);
-  const int w1 = choose_w(slots1, (int)L.nG1, lm[0]), w2 = choose_w(slots2, (int)L.nG2, lm[1]);
+  const int w1 = choose_w(slots1, (int)L.nG1, lm[0], true), w2 = choose_w(slots2, (int)L.nG2, lm[1], false);
   if (w1 == 0 || w2 == 0) return RD_ERR_ARG;  // a fiber does not fit in shared memory
   group_lists_kernel<true><<<grid_for(nrec1), 256, 0, s>>>(g1, at<int32_t>(P, L.gls1), at<uint16_t>(P, L.l1), nullptr);
   group_lists_kernel<true><<<grid_for(nrec2), 256, 0, s>>>(g2, at<int32_t>(P, L.gls2), at<uint16_t>(P, L.l2), nullptr);
