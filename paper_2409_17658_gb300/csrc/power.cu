@@ -314,7 +314,9 @@ rd_status power_search(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, v
   if (e != cudaSuccess) return fail(e);
   // Steps per host check: large products are long enough that one check per
   // step costs nothing; small ones are batched (surplus steps exit at once).
-  const int chunk = (N >= 2048) ? 1 : (N >= 512 ? 4 : 16);
+  // The row-split step (normalised) is about N / 100 times cheaper than the
+  // dense one, so it batches up to larger N.
+  const int chunk = normalised ? (N >= 16384 ? 1 : (N >= 4096 ? 4 : 8)) : (N >= 2048) ? 1 : (N >= 512 ? 4 : 16);
   int enqueued = 1;
   for (;;) {
     e = cudaMemcpyAsync(&h, r.st, sizeof(PowerState), cudaMemcpyDeviceToHost, s);
