@@ -25,7 +25,7 @@ __device__ __forceinline__ unsigned long long chunk_hash(int64_t i, int64_t j0, 
   const unsigned long long lo = (unsigned long long)w[0] | ((unsigned long long)w[1] << 32);
   const unsigned long long hi = (unsigned long long)w[2] | ((unsigned long long)w[3] << 32);
   const unsigned long long pos = ((unsigned long long)i << 32) ^ (unsigned long long)j0;
-  return mix64(mix64(pos ^ lo) ^ hi ^ 0x9E3779B97F4A7C15ull);
+  return mix64(pos ^ lo ^ (hi * 0x9E3779B97F4A7C15ull));
 }
 
 // Lanes e >= valid of a chunk: RD_INF (their contents are padding and must not matter).

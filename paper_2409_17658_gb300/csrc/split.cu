@@ -637,6 +637,7 @@ __global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 4) split_pass_kerne
   uint32_t mv = kInf2;  // pass 1 with norm: halfword minima of the staged values
   unsigned long long hsum = 0;  // pass 2 with norm: hash of the normalised power (as the normaliser's)
   uint32_t nbad = 0;            // pass 2 with norm: a normalised entry left [0, RD_MAX_FINITE]
+  uint32_t fmax = 0;            // pass 2 with norm: halfword maxima of the finite normalised entries
   int32_t mu = 0;
   if (RING && !FIRST && a.norm) {
     const int32_t mr = *(volatile const int32_t*)&a.st->mu;  // complete: pass 1 has finished
@@ -722,18 +723,24 @@ __global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 4) split_pass_kerne
           }
           if (RING && a.norm) {
             // P = R - mu on finite entries, range-checked, hashed per 16-byte chunk as the normaliser does
-            uint32_t hw[4];
+            uint32_t hw[4], sub[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const uint32_t isinf = __vcmpeq2(w4[q], kInf2);
-              const uint32_t sub = __vsub2(w4[q], mu2) & ~isinf;
-              hw[q] = sub | (kInf2 & isinf);
+              sub[q] = __vsub2(w4[q], mu2) & ~isinf;  // 0 in the RD_INF lanes
+              hw[q] = sub[q] | (kInf2 & isinf);
             }
             const int valid = (c + 8 <= a.ncols) ? 8 : (int)(a.ncols - c);
             uint32_t chk[4] = {hw[0], hw[1], hw[2], hw[3]};
-            if (valid < 8) mask_tail(chk, valid);
+            if (valid < 8) {
+              mask_tail(chk, valid);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) nbad |= __vcmpgtu2(chk[q], 0x1FFF1FFFu) & ~__vcmpeq2(chk[q], kInf2);
+              for (int q = 0; q < 4; ++q) nbad |= __vcmpgtu2(chk[q], 0x1FFF1FFFu) & ~__vcmpeq2(chk[q], kInf2);
+            } else {
+              // the range check as a running maximum of the finite entries, tested once at the end
+#pragma unroll
+              for (int q = 0; q < 4; ++q) fmax = __vmaxu2(fmax, sub[q]);
+            }
             hsum += chunk_hash(row, a.out_col0 + c, chk);
 #pragma unroll
             for (int q = 0; q < 4; ++q) w4[q] = hw[q];
@@ -741,7 +748,7 @@ __global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 4) split_pass_kerne
           }
           if (c + 8 <= a.ncols) {
             *reinterpret_cast<uint4*>(out + row * a.ldout + c) = acc[l];
-            m2 = min3(min3(m2, acc[l].x, acc[l].y), acc[l].z, acc[l].w);
+            if (!(RING && a.norm)) m2 = min3(min3(m2, acc[l].x, acc[l].y), acc[l].z, acc[l].w);  // min_out
           } else {
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
@@ -771,6 +778,7 @@ __global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 4) split_pass_kerne
         if (bm < kInf && bm < *(volatile const int32_t*)&a.st->mu) atomicMin(&a.st->mu, bm);
       }
     } else {
+      nbad |= __vcmpgtu2(fmax, 0x1FFF1FFFu);
       for (int o = 16; o > 0; o >>= 1) hsum += __shfl_xor_sync(0xFFFFFFFFu, hsum, o);
       if ((threadIdx.x & 31) == 0) red_h[threadIdx.x >> 5] = hsum;
       const int any_bad = __syncthreads_or(nbad != 0);
