@@ -533,13 +533,14 @@ cudaError_t launch_fill_i32(int32_t* dst, int32_t value, cudaStream_t s) {
 }
 
 // Split K when the output tiles alone fill less than one wave (2 CTAs per SM): S in {2, 4, 8}, the
-// smallest that fills it, with every K slice at least 4 k-tiles deep and none empty.
+// smallest that fills it, with every K slice at least 8 k-tiles deep and none empty.  (Shorter slices
+// measured slower: at N = 1024, 8 slices of 128 took 0.051 ms against 0.045 ms for 4 of 256.)
 int splitk_factor(int64_t tiles, int64_t K) {
   int dev = 0, sms = 148;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t wave = 2 * (int64_t)sms;
   int S = 1;
-  while (S < 8 && tiles * S < wave && K >= (int64_t)(2 * S) * 4 * BK) S *= 2;
+  while (S < 8 && tiles * S < wave && K >= (int64_t)(2 * S) * 8 * BK) S *= 2;
   if (S > 1) {
     const int64_t kslice = ((K + S - 1) / S + BK - 1) / BK * BK;
     while (S > 1 && (int64_t)(S - 1) * kslice >= K) S /= 2;  // every slice non-empty
