@@ -544,12 +544,32 @@ __device__ __forceinline__ void fold_pair(uint4 (&acc)[4], const uint4& v0, cons
   }
 }
 
-// Folds the sub-list [e0, e1) (even bounds) of target set SET into the group's accumulators.
-template <int SET, int LR>
+// Folds the sub-list [e0, e1) (even bounds) of target set SET into the group's accumulators.  SCALED:
+// the list entries are byte offsets of the staged rows (slot x 16 LR, the list as staged in shared
+// memory), so a row's address is one add and one mask or shift away.
+template <int SET, int LR, bool SCALED>
 __device__ __forceinline__ void fold_sublist(uint4 (&acc)[4], const uint4* sm, const uint32_t* pairs, int e0, int e1,
                                              int lane) {
   int p = e0 >> 1;
   const int pe = e1 >> 1;
+  if constexpr (SCALED) {
+    const char* base = reinterpret_cast<const char*>(sm);
+    const uint32_t lane2 = (uint32_t)lane * 16u * 0x00010001u;  // the lane's offset, in both halves
+    for (; p + 2 <= pe; p += 2) {
+      const uint32_t i0 = pairs[p] + lane2, i1 = pairs[p + 1] + lane2;
+      const uint4 v0 = *reinterpret_cast<const uint4*>(base + (i0 & 0xFFFFu));
+      const uint4 v1 = *reinterpret_cast<const uint4*>(base + (i0 >> 16));
+      const uint4 v2 = *reinterpret_cast<const uint4*>(base + (i1 & 0xFFFFu));
+      const uint4 v3 = *reinterpret_cast<const uint4*>(base + (i1 >> 16));
+      fold_pair<SET>(acc, v0, v1);
+      fold_pair<SET>(acc, v2, v3);
+    }
+    if (p < pe) {
+      const uint32_t i0 = pairs[p] + lane2;
+      fold_pair<SET>(acc, *reinterpret_cast<const uint4*>(base + (i0 & 0xFFFFu)),
+                     *reinterpret_cast<const uint4*>(base + (i0 >> 16)));
+    }
+  } else {
   for (; p + 2 <= pe; p += 2) {
     const uint32_t i0 = pairs[p], i1 = pairs[p + 1];
     const uint4 v0 = sm[(int)(i0 & 0xFFFFu) * LR + lane];
@@ -562,6 +582,7 @@ __device__ __forceinline__ void fold_sublist(uint4 (&acc)[4], const uint4* sm, c
   if (p < pe) {
     const uint32_t i0 = pairs[p];
     fold_pair<SET>(acc, sm[(int)(i0 & 0xFFFFu) * LR + lane], sm[(int)(i0 >> 16) * LR + lane]);
+  }
   }
 }
 
@@ -626,7 +647,11 @@ __global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 4) split_pass_kerne
     for (int i = threadIdx.x; i < nb; i += kSplitThreads) sgls[i] = (uint16_t)(__ldg(a.gls + r0 + i) - base);
     for (int i = threadIdx.x; i < a.n_groups; i += kSplitThreads) sgo[i] = __ldg(go4 + i);
     const int npairs = (__ldg(a.gls + r0 + nb) - base) >> 1;
-    for (int i = threadIdx.x; i < npairs; i += kSplitThreads) slst[i] = __ldg(glst + i);
+    constexpr uint32_t kRowBytes = (uint32_t)W * 2;  // staged rows fit in 64 KB (stageable), so offsets fit 16 bits
+    for (int i = threadIdx.x; i < npairs; i += kSplitThreads) {
+      const uint32_t q = __ldg(glst + i);
+      slst[i] = (q & 0xFFFFu) * kRowBytes | ((q >> 16) * kRowBytes) << 16;
+    }
     if (FIRST)
       for (int i = threadIdx.x; i < nst - 1; i += kSplitThreads) smem_words[i] = __ldg(a.fmem + f0 + i);
     for (int i = threadIdx.x; i < a.n_groups; i += kSplitThreads) sord[i] = gord[i];
@@ -699,13 +724,13 @@ __global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 4) split_pass_kerne
         b[0] = q0.x - base; b[1] = q0.y - base; b[2] = q0.z - base; b[3] = q0.w - base;
         b[4] = q1.x - base; b[5] = q1.y - base; b[6] = q1.z - base; b[7] = q1.w - base;
       }
-      fold_sublist<0x1, LR>(acc, sm, pairs, b[0], b[1], lane);
-      fold_sublist<0x4, LR>(acc, sm, pairs, b[1], b[2], lane);
-      fold_sublist<0x5, LR>(acc, sm, pairs, b[2], b[3], lane);
-      fold_sublist<0x6, LR>(acc, sm, pairs, b[3], b[4], lane);
-      fold_sublist<0x7, LR>(acc, sm, pairs, b[4], b[5], lane);
-      fold_sublist<0xC, LR>(acc, sm, pairs, b[5], b[6], lane);
-      fold_sublist<0xD, LR>(acc, sm, pairs, b[6], b[7], lane);
+      fold_sublist<0x1, LR, STAGED>(acc, sm, pairs, b[0], b[1], lane);
+      fold_sublist<0x4, LR, STAGED>(acc, sm, pairs, b[1], b[2], lane);
+      fold_sublist<0x5, LR, STAGED>(acc, sm, pairs, b[2], b[3], lane);
+      fold_sublist<0x6, LR, STAGED>(acc, sm, pairs, b[3], b[4], lane);
+      fold_sublist<0x7, LR, STAGED>(acc, sm, pairs, b[4], b[5], lane);
+      fold_sublist<0xC, LR, STAGED>(acc, sm, pairs, b[5], b[6], lane);
+      fold_sublist<0xD, LR, STAGED>(acc, sm, pairs, b[6], b[7], lane);
       if (!ok) continue;
       const int4 rows = STAGED ? sgo[g] : __ldg(go4 + g);
       const int32_t row4[4] = {rows.x, rows.y, rows.z, rows.w};
@@ -820,12 +845,15 @@ __global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 4) split_pass_kerne
 constexpr size_t kSmemLimit = 220 * 1024;
 
 // Shared memory of a launch: rows and metadata when they fit (staged), else the rows alone.
-// Staging needs the fiber's list positions to fit the uint16 offsets.
-bool stageable(int max_list, size_t bytes, size_t limit) { return max_list <= 0xFFFF && bytes <= limit; }
+// Staging needs the fiber's list positions to fit the uint16 offsets, and the staged rows to fit 64 KB
+// (the staged list holds their byte offsets in 16 bits).
+bool stageable(int max_list, int max_slots, int W, size_t bytes, size_t limit) {
+  return max_list <= 0xFFFF && (size_t)(max_slots + 1) * (size_t)W * 2 <= 65536 && bytes <= limit;
+}
 
 size_t pass_smem(int max_slots, int n_groups, int max_list, int W, bool words, bool* staged) {
   const size_t full = pass_smem_layout(max_slots, n_groups, max_list, W, words).bytes;
-  *staged = stageable(max_list, full, kSmemLimit);
+  *staged = stageable(max_list, max_slots, W, full, kSmemLimit);
   return *staged ? full : (size_t)(max_slots + 1) * (size_t)W * 2;
 }
 
@@ -837,7 +865,8 @@ int choose_w(int max_slots, int n_groups, int max_list, bool words) {
   const size_t limits[3] = {72 * 1024, 112 * 1024, kSmemLimit};
   for (size_t lim : limits)
     for (int w : ws)
-      if (stageable(max_list, pass_smem_layout(max_slots, n_groups, max_list, w, words).bytes, lim)) return w;
+      if (stageable(max_list, max_slots, w, pass_smem_layout(max_slots, n_groups, max_list, w, words).bytes, lim))
+        return w;
   for (size_t lim : limits)
     for (int w : ws)
       if ((size_t)(max_slots + 1) * (size_t)w * 2 <= lim) return w;
