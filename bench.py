@@ -369,8 +369,8 @@ def gemv_leg(rd, torch, B, n: int, reps: int = 20) -> dict:
 
 def gemm_sweep(rd, torch, sizes=(1024, 2048, 4096, 32768)) -> dict:
     """The dense product at the sweep's other sizes (the headline size is the main line): the native
-    autotuner picks the split-K factor per size class (outside the timed region), then CUDA events time
-    the product as a caller launches it."""
+    autotuner picks the output tile and split-K factor per size class (outside the timed region), then
+    CUDA events time the product as a caller launches it."""
     from paper_2409_17658_gb300 import inputs
 
     out = {}
@@ -391,7 +391,7 @@ def gemm_sweep(rd, torch, sizes=(1024, 2048, 4096, 32768)) -> dict:
         ms = e0.elapsed_time(e1) / reps
         gops = float(n) ** 3 / (ms * 1e-3) / 1e9
         out[f"N={n}"] = {"ms": ms, "gops": gops, "frac_of_peak": gops / PEAK_GOPS, "split_k": tuned["p"][0],
-                         "tuner_ms": tuned["ms"]}
+                         "tile": "128x128" if tuned["p"][1] else "128x256", "tuner_ms": tuned["ms"]}
         del A, B, C
         torch.cuda.empty_cache()
     return out

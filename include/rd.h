@@ -489,14 +489,15 @@ rd_status rd_power_until_periodic_noalloc(const int16_t *A_dev, int64_t N, int64
  * (RD_TUNE_SPARSE_R).  The library keeps one process-wide table of entries
  * keyed by (mode, key, aux):
  *   RD_TUNE_GEMM_SPLITK  key = rd_tune_bucket(max(M, N)), aux =
- *                        rd_tune_bucket(K); p[0] = S in {1, 2, 4, 8};
+ *                        rd_tune_bucket(K); p[0] = S in {1, 2, 4, 8},
+ *                        p[1] = output tile 0 (128 x 256) or 1 (128 x 128);
  *   RD_TUNE_SPLIT        key = m, aux = j; p[0..3] = w1, k1, w2, k2 (widths
  *                        32, 64 or 128; slabs per CTA 1..64);
  *   RD_TUNE_SPARSE_R     key = rd_tune_bucket(N), aux = 0; p[0] = R in
  *                        {1, 2, 4, 8};
  * ms is the time the autotuner measured for the entry (informational).
- * rd_minplus_gemm takes S from a matching entry (when S suits the product:
- * every K slice non-empty; else its built-in rule), rd_split_plan takes the
+ * rd_minplus_gemm takes S and the tile from a matching entry (when S suits
+ * the product: every K slice non-empty; else its built-in rule), rd_split_plan takes the
  * widths and slabs per CTA from a matching entry (when the plan's staged rows
  * fit with them; else its built-in choice).  RD_TUNE_SPARSE_R entries are
  * recorded for the caller, who passes R to the sparse calls.  The autotuners
@@ -532,12 +533,14 @@ rd_status rd_tune_get(rd_tune_entry_t *entries, int cap, int *count);
 rd_status rd_tune_lookup(int mode, int key, int aux, rd_tune_entry_t *out);
 
 /*
- * rd_tune_gemm -- autotuner for the split-K factor of rd_minplus_gemm on an
- * M x N x K product (operands as in rd_minplus_gemm, M >= 2; C is
- * overwritten): times each S in {1, 2, 4, 8} that suits the product and
- * would not exceed four waves of CTAs (one warm-up, then reps >= 1 timed
- * products), records the fastest in the table (replacing an entry with the
- * same key) and returns it in *best (nullable).  Synchronous.
+ * rd_tune_gemm -- autotuner for the output tile and split-K factor of
+ * rd_minplus_gemm on an M x N x K product (operands as in rd_minplus_gemm,
+ * M >= 2; C is overwritten): times each tile (128 x 256; 128 x 128 for
+ * products of at most four waves of its CTAs) with each S in {1, 2, 4, 8}
+ * that suits the product and would not exceed four waves of CTAs (one
+ * warm-up, then reps >= 1 timed products), records the fastest in the table
+ * (replacing an entry with the same key) and returns it in *best (nullable).
+ * Synchronous.
  */
 rd_status rd_tune_gemm(const int16_t *A, int64_t lda, const int16_t *B, int64_t ldb, int16_t *C, int64_t ldc,
                        int64_t M, int64_t N, int64_t K, int reps, rd_tune_entry_t *best, cudaStream_t s);

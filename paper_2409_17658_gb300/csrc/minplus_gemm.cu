@@ -36,6 +36,10 @@ constexpr int kGroupM = 16;  // row tiles per rasterisation group
 constexpr int AS_WORDS = BK * BM;         // one A^T buffer, duplicated int16 -> 32-bit words
 constexpr int BS_WORDS = BK * (BN / 2);   // one B stage, packed int16 pairs
 constexpr size_t SMEM_BYTES = (size_t)(2 * AS_WORDS + BSTAGES * BS_WORDS) * 4;
+// The narrow tile (BM x 128) for products with few output tiles: half the columns per thread, so twice
+// the CTAs over the same product, and shared memory for three CTAs per SM.
+constexpr int BN_NARROW = 128;
+constexpr size_t smem_bytes(int bn) { return (size_t)(2 * AS_WORDS + BSTAGES * BK * (bn / 2)) * 4; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -56,14 +60,19 @@ __device__ __forceinline__ uint32_t pack2(int16_t lo, int16_t hi) {
 // One BM x BN output tile of C = A (x) B at (m0, n0), plus its contribution to the
 // minimum (min_out) and the diagonal minimum (diag_out) when those are not null.  SPLIT: the tile
 // of this CTA's K slice is left in shared memory ([BM][BN/2] packed words) for a cluster reduction.
-template <bool SPLIT = false>
+template <bool SPLIT = false, int BNT = BN>
 __device__ __forceinline__ void gemm_tile(const int16_t* __restrict__ Ag, const int16_t* __restrict__ Bg,
                                           int16_t* __restrict__ Cg, const int64_t M, const int64_t N,
                                           const int64_t K, const int64_t lda, const int64_t ldb, const int64_t ldc,
                                           const int64_t m0, const int64_t n0, int32_t* min_out, int32_t* diag_out,
                                           uint32_t* smem) {
+  constexpr int BSW = BK * (BNT / 2);  // one B stage, in words
+  constexpr int NBC = BNT / 64;        // 16-byte chunks of a B stage per thread
+  constexpr int CPR = BNT / 8;         // 16-byte chunks per B row
+  constexpr int NV = BNT / 32;         // accumulator words per row of a thread (BNT / 16 columns)
+  constexpr int PARTS = BNT / 128;     // 128-column parts of a thread's columns
   uint32_t* As = smem;                 // [2][BK][BM]
-  uint32_t* Bs = smem + 2 * AS_WORDS;  // [BSTAGES][BK][BN/2]
+  uint32_t* Bs = smem + 2 * AS_WORDS;  // [BSTAGES][BK][BNT/2]
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int KT = (int)((K + BK - 1) / BK);
 
@@ -71,19 +80,19 @@ __device__ __forceinline__ void gemm_tile(const int16_t* __restrict__ Ag, const 
   uint4 areg[2];
   // Interior tiles (all rows and columns inside C) over whole k-tiles take the unchecked
   // path: per-thread source pointers computed once, no per-chunk bounds arithmetic.
-  const bool full_mn = (m0 + BM <= M) && (n0 + BN <= N);
+  const bool full_mn = (m0 + BM <= M) && (n0 + BNT <= N);
   const int kt_full = (int)(K / BK);
   const int16_t* a_src[2];
-  const int16_t* b_src[4];
+  const int16_t* b_src[NBC];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int c = tid + h * NT;
     a_src[h] = Ag + (m0 + (c >> 2)) * lda + (c & 3) * 8;
   }
 #pragma unroll
-  for (int h = 0; h < 4; ++h) {
+  for (int h = 0; h < NBC; ++h) {
     const int c = tid + h * NT;
-    b_src[h] = Bg + (int64_t)(c >> 5) * ldb + n0 + (c & 31) * 8;
+    b_src[h] = Bg + (int64_t)(c / CPR) * ldb + n0 + (c % CPR) * 8;
   }
   const int64_t b_step = (int64_t)BK * ldb;
 
@@ -121,20 +130,20 @@ __device__ __forceinline__ void gemm_tile(const int16_t* __restrict__ Ag, const 
     }
   };
   auto load_b_stage = [&](int kt, int stage) {
-    uint32_t* dst = Bs + stage * BS_WORDS;
+    uint32_t* dst = Bs + stage * BSW;
     if (full_mn && kt < kt_full) {
 #pragma unroll
-      for (int h = 0; h < 4; ++h) {
+      for (int h = 0; h < NBC; ++h) {
         const int c = tid + h * NT;
-        cp_async16(dst + (c >> 5) * (BN / 2) + (c & 31) * 4, b_src[h] + (int64_t)kt * b_step);
+        cp_async16(dst + (c / CPR) * (BNT / 2) + (c % CPR) * 4, b_src[h] + (int64_t)kt * b_step);
       }
       return;
     }
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      const int c = tid + h * NT, kr = c >> 5, jc = (c & 31) * 8;
+    for (int h = 0; h < NBC; ++h) {
+      const int c = tid + h * NT, kr = c / CPR, jc = (c % CPR) * 8;
       const int64_t gk = (int64_t)kt * BK + kr, gj = n0 + jc;
-      uint32_t* d = dst + kr * (BN / 2) + jc / 2;
+      uint32_t* d = dst + kr * (BNT / 2) + jc / 2;
       if (gk < K && gj + 8 <= N) {
         cp_async16(d, Bg + gk * ldb + gj);
       } else {
@@ -147,11 +156,11 @@ __device__ __forceinline__ void gemm_tile(const int16_t* __restrict__ Ag, const 
     }
   };
 
-  uint32_t acc[8][8];
+  uint32_t acc[8][NV];
 #pragma unroll
   for (int r = 0; r < 8; ++r)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[r][c] = kInf2;
+    for (int c = 0; c < NV; ++c) acc[r][c] = kInf2;
 
   // ---- prologue
 #pragma unroll
@@ -175,19 +184,25 @@ __device__ __forceinline__ void gemm_tile(const int16_t* __restrict__ Ag, const 
       cp_async_commit();
     }
     const uint32_t* a_s = As + (kt & 1) * AS_WORDS + ty * 8;
-    const uint32_t* b_s = Bs + (kt % BSTAGES) * BS_WORDS + tx * 4;
+    const uint32_t* b_s = Bs + (kt % BSTAGES) * BSW + tx * 4;
 #pragma unroll 8
     for (int kk = 0; kk < BK; ++kk) {
       const uint4 a0 = *reinterpret_cast<const uint4*>(a_s + kk * BM);
       const uint4 a1 = *reinterpret_cast<const uint4*>(a_s + kk * BM + 4);
-      const uint4 b0 = *reinterpret_cast<const uint4*>(b_s + kk * (BN / 2));
-      const uint4 b1 = *reinterpret_cast<const uint4*>(b_s + kk * (BN / 2) + 64);
       const uint32_t a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const uint32_t b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+      uint32_t b[NV];
+#pragma unroll
+      for (int part = 0; part < PARTS; ++part) {
+        const uint4 bp = *reinterpret_cast<const uint4*>(b_s + kk * (BNT / 2) + part * 64);
+        b[part * 4] = bp.x;
+        b[part * 4 + 1] = bp.y;
+        b[part * 4 + 2] = bp.z;
+        b[part * 4 + 3] = bp.w;
+      }
 #pragma unroll
       for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[r][c] = __viaddmin_s16x2(a[r], b[c], acc[r][c]);
+        for (int c = 0; c < NV; ++c) acc[r][c] = __viaddmin_s16x2(a[r], b[c], acc[r][c]);
     }
     if (kt + 1 < KT) {
       store_a_smem((kt + 1) & 1);
@@ -204,8 +219,8 @@ __device__ __forceinline__ void gemm_tile(const int16_t* __restrict__ Ag, const 
 #pragma unroll
     for (int r = 0; r < 8; ++r)
 #pragma unroll
-      for (int part = 0; part < 2; ++part)
-        T[(ty * 8 + r) * (BN / 8) + part * 16 + tx] =
+      for (int part = 0; part < PARTS; ++part)
+        T[(ty * 8 + r) * (BNT / 8) + part * 16 + tx] =
             make_uint4(acc[r][part * 4], acc[r][part * 4 + 1], acc[r][part * 4 + 2], acc[r][part * 4 + 3]);
     return;
   }
@@ -213,12 +228,12 @@ __device__ __forceinline__ void gemm_tile(const int16_t* __restrict__ Ag, const 
   // ---- epilogue: store, and reduce the minimum and the diagonal minimum
   uint32_t vmin = kInf2;
   int32_t dmin = kInf;
-  const bool want_diag = (diag_out != nullptr) && (m0 < n0 + BN) && (n0 < m0 + BM);
+  const bool want_diag = (diag_out != nullptr) && (m0 < n0 + BNT) && (n0 < m0 + BM);
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     const int64_t gi = m0 + ty * 8 + r;
 #pragma unroll
-    for (int part = 0; part < 2; ++part) {
+    for (int part = 0; part < PARTS; ++part) {
       const int64_t gj = n0 + part * 128 + tx * 8;
       const uint32_t* w = &acc[r][part * 4];
 #pragma unroll
@@ -276,8 +291,8 @@ __device__ __forceinline__ void grouped_tile(int64_t linear, int64_t gx, int64_t
   *tile_n = in_group / group_rows;
 }
 
-template <bool RING>
-__global__ void __launch_bounds__(NT, 2) minplus_gemm_kernel(GemmParams p) {
+template <bool RING, int BNT = BN>
+__global__ void __launch_bounds__(NT, BNT == BN ? 2 : 3) minplus_gemm_kernel(GemmParams p) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int16_t* Ag = p.A;
   int16_t* Cg = p.C;
@@ -290,33 +305,35 @@ __global__ void __launch_bounds__(NT, 2) minplus_gemm_kernel(GemmParams p) {
   }
   int64_t tm, tn;
   grouped_tile((int64_t)blockIdx.y * gridDim.x + blockIdx.x, gridDim.x, gridDim.y, &tm, &tn);
-  gemm_tile(Ag, p.B, Cg, p.M, p.N, p.K, p.lda, p.ldb, p.ldc, tm * BM, tn * BN, p.min_out, p.diag_out, smem);
+  gemm_tile<false, BNT>(Ag, p.B, Cg, p.M, p.N, p.K, p.lda, p.ldb, p.ldc, tm * BM, tn * BNT, p.min_out, p.diag_out,
+                        smem);
 }
 
 // ---- split K for small products: a cluster of S CTAs per output tile, CTA r computing the tile over
 // its K slice [r kslice, (r + 1) kslice); the S partial tiles, left in the CTAs' shared memory, meet in
 // distributed shared memory, CTA r min-reducing rows [r BM/S, (r + 1) BM/S) of the tile and writing
 // them (with the minimum).  Used when the output tiles alone would not fill one wave of the GPU.
-__global__ void __launch_bounds__(NT, 2) minplus_gemm_splitk_kernel(GemmParams p, int64_t kslice) {
+template <int BNT>
+__global__ void __launch_bounds__(NT, BNT == BN ? 2 : 3) minplus_gemm_splitk_kernel(GemmParams p, int64_t kslice) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) uint32_t smem[];
   const int rank = (int)cluster.block_rank(), S = (int)cluster.num_blocks();
   int64_t tm, tn;
   grouped_tile((int64_t)blockIdx.y * gridDim.x + blockIdx.x, gridDim.x, gridDim.y, &tm, &tn);
-  const int64_t m0 = tm * BM, n0 = tn * BN;
+  const int64_t m0 = tm * BM, n0 = tn * BNT;
   const int64_t k0 = (int64_t)rank * kslice, k1 = (k0 + kslice < p.K) ? k0 + kslice : p.K;
-  gemm_tile<true>(p.A + k0, p.B + k0 * p.ldb, nullptr, p.M, p.N, k1 - k0, p.lda, p.ldb, p.ldc, m0, n0, nullptr,
-                  nullptr, smem);
+  gemm_tile<true, BNT>(p.A + k0, p.B + k0 * p.ldb, nullptr, p.M, p.N, k1 - k0, p.lda, p.ldb, p.ldc, m0, n0, nullptr,
+                       nullptr, smem);
   cluster.sync();  // every partial tile is in place
   const int rows = BM / S;
   uint32_t vmin = kInf2;
   int32_t emin = kInf;
-  for (int v = threadIdx.x; v < rows * (BN / 8); v += NT) {
-    const int row = rank * rows + v / (BN / 8), c8 = v % (BN / 8);
+  for (int v = threadIdx.x; v < rows * (BNT / 8); v += NT) {
+    const int row = rank * rows + v / (BNT / 8), c8 = v % (BNT / 8);
     uint4 r = make_uint4(kInf2, kInf2, kInf2, kInf2);
     for (int q = 0; q < S; ++q) {
-      const uint4 t = cluster.map_shared_rank(reinterpret_cast<uint4*>(smem), q)[row * (BN / 8) + c8];
+      const uint4 t = cluster.map_shared_rank(reinterpret_cast<uint4*>(smem), q)[row * (BNT / 8) + c8];
       r = make_uint4(__vmins2(r.x, t.x), __vmins2(r.y, t.y), __vmins2(r.z, t.z), __vmins2(r.w, t.w));
     }
     // the tile's word w covers columns 2w, 2w + 1: vector c8 = part * 16 + tx holds part * 128 + tx * 8 ..
@@ -504,7 +521,7 @@ __global__ void __launch_bounds__(kGemvThreads) minplus_gemv_kernel(const int16_
   }
 }
 
-template <int WHICH>  // 0 plain, 1 ring, 2 batched
+template <int WHICH>  // 0 plain, 1 ring, 2 batched, 3 split K, 4 plain narrow, 5 split K narrow
 cudaError_t set_smem_attr() {
   static int done_dev[64] = {0};
   int dev = 0;
@@ -516,8 +533,14 @@ cudaError_t set_smem_attr() {
   else if (WHICH == 1)
     e = cudaFuncSetAttribute(minplus_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
   else if (WHICH == 3)
-    e = cudaFuncSetAttribute(minplus_gemm_splitk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(minplus_gemm_splitk_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)SMEM_BYTES);
+  else if (WHICH == 4)
+    e = cudaFuncSetAttribute(minplus_gemm_kernel<false, BN_NARROW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes(BN_NARROW));
+  else if (WHICH == 5)
+    e = cudaFuncSetAttribute(minplus_gemm_splitk_kernel<BN_NARROW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes(BN_NARROW));
   else
     e = cudaFuncSetAttribute(minplus_gemm_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)SMEM_BYTES);
@@ -557,32 +580,39 @@ bool splitk_suits(int S, int64_t K) {
 
 int64_t gemm_tiles(int64_t M, int64_t N) { return ((M + BM - 1) / BM) * ((N + BN - 1) / BN); }
 
-cudaError_t launch_minplus_gemm(const GemmParams& p, bool ring, cudaStream_t s, int force_splitk) {
-  const int64_t gx = (p.N + BN - 1) / BN, gy = (p.M + BM - 1) / BM;
+cudaError_t launch_minplus_gemm(const GemmParams& p, bool ring, cudaStream_t s, int force_splitk, int force_tile) {
+  int S = 1;     // ring mode and the diagonal output keep one CTA per tile (no diagonal in the split form)
+  int tile = 0;  // 0: BM x BN, 1: BM x BN_NARROW (no ring mode, no diagonal)
+  if (force_splitk > 0) {
+    if (ring || p.diag_out != nullptr || !splitk_suits(force_splitk, p.K) || force_tile < 0 || force_tile > 1)
+      return cudaErrorInvalidValue;
+    S = force_splitk;
+    tile = force_tile;
+  } else if (!ring && p.diag_out == nullptr) {
+    rd_tune_entry_t t;
+    const int64_t mn = p.M > p.N ? p.M : p.N;
+    if (tune_find(RD_TUNE_GEMM_SPLITK, rd_tune_bucket(mn), rd_tune_bucket(p.K), &t) && splitk_suits(t.p[0], p.K)) {
+      S = t.p[0];
+      tile = t.p[1];
+    } else {
+      S = splitk_factor(gemm_tiles(p.M, p.N), p.K);
+    }
+  }
+  const int bn = tile ? BN_NARROW : BN;
+  const size_t smem = tile ? smem_bytes(BN_NARROW) : SMEM_BYTES;
+  const int64_t gx = (p.N + bn - 1) / bn, gy = (p.M + BM - 1) / BM;
   if (gx <= 0 || gy <= 0) return cudaSuccess;
   if (gx > 0x7FFFFFFF || gy > 65535) return cudaErrorInvalidConfiguration;
   const dim3 grid((unsigned)gx, (unsigned)gy);
   cudaError_t e;
-  int S = 1;  // ring mode and the diagonal output keep one CTA per tile (no diagonal in the split form)
-  if (force_splitk > 0) {
-    if (ring || p.diag_out != nullptr || !splitk_suits(force_splitk, p.K)) return cudaErrorInvalidValue;
-    S = force_splitk;
-  } else if (!ring && p.diag_out == nullptr) {
-    rd_tune_entry_t t;
-    const int64_t mn = p.M > p.N ? p.M : p.N;
-    if (tune_find(RD_TUNE_GEMM_SPLITK, rd_tune_bucket(mn), rd_tune_bucket(p.K), &t) && splitk_suits(t.p[0], p.K))
-      S = t.p[0];
-    else
-      S = splitk_factor(gx * gy, p.K);
-  }
   if (S > 1) {
-    e = set_smem_attr<3>();
+    e = tile ? set_smem_attr<5>() : set_smem_attr<3>();
     if (e != cudaSuccess) return e;
     const int64_t kslice = ((p.K + S - 1) / S + BK - 1) / BK * BK;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)gx, (unsigned)gy, (unsigned)S);
     cfg.blockDim = dim3(NT, 1, 1);
-    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -591,7 +621,8 @@ cudaError_t launch_minplus_gemm(const GemmParams& p, bool ring, cudaStream_t s, 
     attr[0].val.clusterDim.z = (unsigned)S;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, minplus_gemm_splitk_kernel, p, kslice);
+    e = tile ? cudaLaunchKernelEx(&cfg, minplus_gemm_splitk_kernel<BN_NARROW>, p, kslice)
+             : cudaLaunchKernelEx(&cfg, minplus_gemm_splitk_kernel<BN>, p, kslice);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
@@ -599,6 +630,10 @@ cudaError_t launch_minplus_gemm(const GemmParams& p, bool ring, cudaStream_t s, 
     e = set_smem_attr<1>();
     if (e != cudaSuccess) return e;
     minplus_gemm_kernel<true><<<grid, NT, SMEM_BYTES, s>>>(p);
+  } else if (tile) {
+    e = set_smem_attr<4>();
+    if (e != cudaSuccess) return e;
+    minplus_gemm_kernel<false, BN_NARROW><<<grid, NT, smem, s>>>(p);
   } else {
     e = set_smem_attr<0>();
     if (e != cudaSuccess) return e;

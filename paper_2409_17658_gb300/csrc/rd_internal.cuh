@@ -79,9 +79,11 @@ struct GemmParams {
 };
 
 // Launchers implemented in the .cu files.
-// force_splitk > 0 (not in ring mode): split K by exactly that factor (the autotuner's trials); else the
-// tuning table's factor for the product's size class, else the built-in rule.
-cudaError_t launch_minplus_gemm(const GemmParams& p, bool ring, cudaStream_t s, int force_splitk = 0);
+// force_splitk > 0 (not in ring mode): split K by exactly that factor, with tile shape force_tile (0: 128 x
+// 256, 1: 128 x 128) -- the autotuner's trials; else the tuning table's factor and tile for the product's
+// size class, else the built-in rule (the wide tile).
+cudaError_t launch_minplus_gemm(const GemmParams& p, bool ring, cudaStream_t s, int force_splitk = 0,
+                                int force_tile = 0);
 bool splitk_suits(int S, int64_t K);         // S in {1, 2, 4, 8} and every K slice non-empty
 int64_t gemm_tiles(int64_t M, int64_t N);  // output tiles (CTAs of an unsplit launch)
 

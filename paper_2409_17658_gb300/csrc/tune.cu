@@ -1,6 +1,6 @@
 // tune.cu -- the tuning table and the autotuners of the launch shapes.
 //
-// A launch shape (the split-K factor of the dense product, the slab widths and slabs per CTA of the
+// A launch shape (the output tile and split-K factor of the dense product, the slab widths and slabs per CTA of the
 // row-split passes, the rows per block of the sparse step) changes how long a product takes, never
 // what it computes.  The table maps (mode, size class) to the shape the autotuner measured fastest
 // on this GPU; the launchers consult it and fall back to their built-in rules.  The table is one
@@ -33,7 +33,8 @@ bool is_pow2_le8(int v) { return v == 1 || v == 2 || v == 4 || v == 8; }
 bool entry_ok(const rd_tune_entry_t& t) {
   switch (t.mode) {
     case RD_TUNE_GEMM_SPLITK:
-      return t.key >= 0 && t.key <= 63 && t.aux >= 0 && t.aux <= 63 && is_pow2_le8(t.p[0]);
+      return t.key >= 0 && t.key <= 63 && t.aux >= 0 && t.aux <= 63 && is_pow2_le8(t.p[0]) &&
+             (t.p[1] == 0 || t.p[1] == 1);
     case RD_TUNE_SPLIT:
       return t.key >= 2 && t.key <= RD_MAX_M && t.aux >= 1 && t.aux < t.key &&
              (t.p[0] == 32 || t.p[0] == 64 || t.p[0] == 128) && t.p[1] >= 1 && t.p[1] <= 64 &&
@@ -153,7 +154,7 @@ extern "C" rd_status rd_tune_gemm(const int16_t* A, int64_t lda, const int16_t* 
   if (lda < K || lda % 8 != 0 || ldb < N || ldb % 8 != 0 || ldc < N || ldc % 8 != 0) return RD_ERR_ARG;
   int dev = 0, sms = 148;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t tiles = gemm_tiles(M, N), wave = 2 * (int64_t)sms;
+  const int64_t tiles_wide = gemm_tiles(M, N), tiles_narrow = ((M + 127) / 128) * ((N + 127) / 128);
   Events ev;
   cudaError_t ce = ev.create();
   if (ce != cudaSuccess) {
@@ -176,23 +177,29 @@ extern "C" rd_status rd_tune_gemm(const int16_t* A, int64_t lda, const int16_t* 
   t.aux = rd_tune_bucket(K);
   t.ms = -1.f;
   const int cands[4] = {1, 2, 4, 8};
-  for (int S : cands) {
-    if (!splitk_suits(S, K) || (S > 1 && tiles * S > 4 * wave)) continue;
-    rd_status rc = RD_OK;
-    const float ms = time_calls(
-        [&]() -> rd_status {
-          const cudaError_t e = launch_minplus_gemm(p, false, s, S);
-          if (e != cudaSuccess) {
-            set_cuda_error(e);
-            return RD_ERR_CUDA;
-          }
-          return RD_OK;
-        },
-        reps, ev.e0, ev.e1, s, &rc);
-    if (rc != RD_OK) return rc;
-    if (t.ms < 0.f || ms < t.ms) {
-      t.p[0] = S;
-      t.ms = ms;
+  for (int tile = 0; tile < 2; ++tile) {
+    // the wide tile runs 2 CTAs per SM, the narrow one 3
+    const int64_t tiles = tile ? tiles_narrow : tiles_wide, wave = (tile ? 3 : 2) * (int64_t)sms;
+    for (int S : cands) {
+      if (!splitk_suits(S, K) || (S > 1 && tiles * S > 4 * wave)) continue;
+      if (tile && tiles > 4 * wave) continue;  // the narrow tile only for products of a few waves
+      rd_status rc = RD_OK;
+      const float ms = time_calls(
+          [&]() -> rd_status {
+            const cudaError_t e = launch_minplus_gemm(p, false, s, S, tile);
+            if (e != cudaSuccess) {
+              set_cuda_error(e);
+              return RD_ERR_CUDA;
+            }
+            return RD_OK;
+          },
+          reps, ev.e0, ev.e1, s, &rc);
+      if (rc != RD_OK) return rc;
+      if (t.ms < 0.f || ms < t.ms) {
+        t.p[0] = S;
+        t.p[1] = tile;
+        t.ms = ms;
+      }
     }
   }
   if (!tune_put(t)) return RD_ERR_NOMEM;  // the table is full

@@ -42,8 +42,10 @@ def upload(torch, host):
     return t.cuda()
 
 
+@pytest.mark.parametrize("tile", [0, 1])
 @pytest.mark.parametrize("S", [1, 2, 4, 8])
-def test_gemm_reads_its_split_factor_from_the_table(rd, orc, S):
+def test_gemm_reads_its_split_factor_from_the_table(rd, orc, S, tile):
+    """Every split factor with both output tiles (128 x 256 and 128 x 128), on a ragged product."""
     import torch
     from paper_2409_17658_gb300 import inputs
 
@@ -52,7 +54,7 @@ def test_gemm_reads_its_split_factor_from_the_table(rd, orc, S):
     b = inputs.matrix(K, N, seed=42, dist="wide")
     A, B = upload(torch, a), upload(torch, b)
     C = torch.full((M, B.shape[1]), 777, dtype=torch.int16, device="cuda")
-    rd.tune_set([dict(mode="gemm_splitk", key=rd.tune_bucket(max(M, N)), aux=rd.tune_bucket(K), p=[S, 0, 0, 0])])
+    rd.tune_set([dict(mode="gemm_splitk", key=rd.tune_bucket(max(M, N)), aux=rd.tune_bucket(K), p=[S, tile, 0, 0])])
     mn = torch.zeros(1, dtype=torch.int32, device="cuda")
     rd.minplus_gemm(A, B, C, M, N, K, min_out=mn)
     want = orc.minplus_i16(a, b)
@@ -86,10 +88,35 @@ def test_tune_gemm_records_the_fastest_factor(rd, orc):
     C = torch.empty((n, n), dtype=torch.int16, device="cuda")
     e = rd.tune_gemm(A, B, C, reps=3)
     assert e["mode"] == "gemm_splitk" and e["key"] == 10 and e["aux"] == 10 and e["p"][0] in (1, 2, 4, 8)
+    assert e["p"][1] in (0, 1)
     assert e["ms"] > 0 and rd.tune_table() == [e]
     rd.minplus_gemm(A, B, C)  # with the recorded factor
     a, b = A.cpu().numpy(), B.cpu().numpy()
     assert np.array_equal(C.cpu().numpy().astype(np.int32), orc.minplus_i16(a, b))
+
+
+@pytest.mark.parametrize("n", [1024, 2048])
+def test_narrow_tile_at_sweep_sizes(rd, orc, n):
+    """The 128 x 128 tile (no split and split by 4) on the sweep's small sizes: all entries against the oracle."""
+    import torch
+    from paper_2409_17658_gb300 import inputs
+
+    A = inputs.matrix_torch(n, n, seed=5, dist="wide", device="cuda")
+    B = inputs.matrix_torch(n, n, seed=6, dist="wide", device="cuda")
+    a, b = A.cpu().numpy(), B.cpu().numpy()
+    want = orc.minplus_i16(a, b) if n <= 1024 else None
+    rng = np.random.default_rng(n)
+    ri, cj = rng.integers(0, n, 256), rng.integers(0, n, 256)
+    for S in (1, 4):
+        rd.tune_set([dict(mode="gemm_splitk", key=rd.tune_bucket(n), aux=rd.tune_bucket(n), p=[S, 1, 0, 0])])
+        C = torch.empty((n, n), dtype=torch.int16, device="cuda")
+        mn = torch.zeros(1, dtype=torch.int32, device="cuda")
+        rd.minplus_gemm(A, B, C, min_out=mn)
+        got = C.cpu().numpy().astype(np.int32)
+        if want is not None:
+            assert np.array_equal(got, want) and mn.item() == want.min(), S
+        else:
+            assert np.array_equal(got[ri, cj], orc.minplus_i16_entries(a, b, ri, cj)), S
 
 
 def test_tune_gemm_argument_checks(rd):

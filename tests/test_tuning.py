@@ -46,6 +46,7 @@ def test_set_get_lookup_round_trip(rd):
     dict(mode=9, key=1, aux=0, p=[1]),                       # unknown mode
     dict(mode="gemm_splitk", key=10, aux=10, p=[3]),         # S not in {1, 2, 4, 8}
     dict(mode="gemm_splitk", key=10, aux=10, p=[16]),
+    dict(mode="gemm_splitk", key=10, aux=10, p=[2, 2]),        # tile 0 or 1
     dict(mode="split", key=9, aux=9, p=[64, 8, 64, 8]),      # j must be < m
     dict(mode="split", key=1, aux=0, p=[64, 8, 64, 8]),      # m >= 2
     dict(mode="split", key=9, aux=4, p=[96, 8, 64, 8]),      # width not 32, 64 or 128
