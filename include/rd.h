@@ -110,6 +110,12 @@ rd_status rd_build_transfer_loss(int m, int16_t *A_dev, int64_t lda, cudaStream_
  * gives an all-RD_INF C).  Runs on the DPX add-min units (__viaddmin_s16x2).
  * min_out, if not null, is a device int32 that receives min_ij C[i][j]
  * (RD_INF when C has no finite entry); it is written by this call.
+ * M = 1 goes to rd_minplus_gemv.  Products whose 128 x 256 output tiles fill
+ * less than one wave of the GPU split K across a thread-block cluster (2, 4
+ * or 8 CTAs per tile, partial tiles combined in distributed shared memory);
+ * an RD_TUNE_GEMM_SPLITK entry of the tuning table (below) for the product's
+ * size class chooses the split and the output tile (128 x 256 or 128 x 128)
+ * instead.  The result does not depend on either choice.
  * RD_ERR_ARG for bad sizes, strides or alignment.
  */
 rd_status rd_minplus_gemm(const int16_t *A, int64_t lda, const int16_t *B, int64_t ldb, int16_t *C, int64_t ldc,
