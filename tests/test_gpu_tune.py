@@ -195,3 +195,23 @@ def test_sparse_tune_records_its_r(rd):
     best, ms = rd.sparse_tune(A, n, work)
     e = rd.tune_lookup(rd.RD_TUNE_SPARSE_R, rd.tune_bucket(n), 0)
     assert e is not None and e["p"][0] == best and best in ms
+
+
+def test_server_with_tuned_split_shapes(rd, orc):
+    """A server whose m = 8 and m = 9 jobs build their row-split plans from tuning-table shapes (narrow slabs,
+    one slab per CTA) answers as the oracle's relation says (m = 8) and as Table 2 implies (m = 9)."""
+    rd.tune_set([dict(mode="split", key=8, aux=4, p=[32, 1, 32, 1]), dict(mode="split", key=9, aux=4, p=[64, 2, 32, 4])])
+    ns = np.arange(3, 61, dtype=np.int64)
+    ms = np.array([8] * len(ns) + [9] * len(ns), dtype=np.int32)
+    with rd.Server(hbm_budget_bytes=64 << 30, kmax=64) as sv:
+        g, st, _ = sv.wait(sv.submit(ms, np.concatenate([ns, ns])), timeout_s=600)
+    assert np.all(st == rd.RD_OK)
+    o8 = orc.power_until_periodic(8, kmax=48)
+    want8 = [orc.gamma_from_period(o8["gamma"], o8["k"], o8["p"], o8["q"], int(n)) for n in ns]
+    assert list(g[:len(ns)]) == want8
+    # m = 9: Table 2's relation (22, 5, 20) and Remark 13 (gamma = 2(m + 1)n/5 for n = 0 mod 5)
+    g9 = dict(zip(ns.tolist(), g[len(ns):].tolist()))
+    for n in range(30, 61):
+        assert g9[n] == g9[n - 5] + 20, n
+    for n in range(5, 61, 5):
+        assert 5 * g9[n] == 2 * 10 * n, n
