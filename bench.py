@@ -398,7 +398,7 @@ def gemm_sweep(rd, torch, sizes=(1024, 2048, 4096, 32768)) -> dict:
 
 
 def batched_products(rd, torch, count: int = 64, seed: int = 4) -> dict:
-    """Config of 64 independent products, N_i = round(exp(U[ln 128, ln 8192])) (seeded): one persistent
+    """64 independent products, N_i = round(exp(U[ln 128, ln 8192])) (seeded): one persistent
     batched launch against one launch per product, both on the same stream, results compared."""
     from paper_2409_17658_gb300 import inputs
 

@@ -524,7 +524,7 @@ def test_sparse_minplus_tma(rd, torch_mod, orc, shape, R):
     assert mn.item() == want.min()
 
 
-# ---------------------------------------------------------------- vector x matrix (config 3's GEMV form)
+# ---------------------------------------------------------------- vector x matrix (one row against an N x N operand)
 
 @pytest.mark.parametrize("K,N", [(1, 1), (5, 13), (300, 1000), (9000, 777), (8192, 264), (20000, 2049)])
 def test_minplus_gemv(rd, torch_mod, orc, K, N):
