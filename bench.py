@@ -319,6 +319,32 @@ def run_sparse_only(rd, torch, args) -> None:
                       "b_row_TBps": plan["entries"] * n * 2 / (ms * 1e-3) / 1e12}))
 
 
+def run_batched_only(rd, torch, args) -> None:
+    """The 64-product batch alone: `--warmup` untimed batched launches, then `--steps` timed ones."""
+    from paper_2409_17658_gb300 import inputs
+
+    sizes = inputs.log_uniform_sizes(64, 128, 8192, seed=4)
+    probs = []
+    for i, n in enumerate(sizes):
+        ld = (n + 7) // 8 * 8
+        A = inputs.matrix_torch(n, n, seed=1000 + 2 * i, ld=ld, device="cuda")
+        B = inputs.matrix_torch(n, n, seed=1001 + 2 * i, ld=ld, device="cuda")
+        probs.append((A, B, torch.empty_like(A), n, n, n))
+    for _ in range(args.warmup):
+        rd.minplus_gemm_batched(probs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        rd.minplus_gemm_batched(probs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    ops = float(sum(n ** 3 for n in sizes))
+    print(json.dumps({"batched_only": len(sizes), "ms": ms, "gops": ops / (ms * 1e-3) / 1e9,
+                      "frac_of_peak": ops / (ms * 1e-3) / 1e9 / PEAK_GOPS}))
+
+
 def run_split_only(rd, torch, args) -> None:
     """One row-split product A(G) (x) P with P = A(G)^2, repeated: the kernel pair of the power step."""
     m = args.split_only
@@ -574,6 +600,7 @@ def main() -> None:
     ap.add_argument("--split-only", type=int, default=0, metavar="M",
                     help="time only the row-split product at m = M (profiling aid)")
     ap.add_argument("--tune", action="store_true", help="with --split-only: run the autotuner on the plan first")
+    ap.add_argument("--batched-only", action="store_true", help="time only the 64-product batch (profiling aid)")
     ap.add_argument("--tune-table", default="", metavar="PATH",
                     help="load a saved tuning table (JSON, paper_2409_17658_gb300.tuning) before running")
     ap.add_argument("--no-sweep", action="store_true", help="skip the dense sweep at the other sizes")
@@ -597,6 +624,8 @@ def main() -> None:
         return run_sparse_only(rd, torch, args)
     if args.split_only:
         return run_split_only(rd, torch, args)
+    if args.batched_only:
+        return run_batched_only(rd, torch, args)
     if args.gemv_only:
         from paper_2409_17658_gb300 import inputs
 
