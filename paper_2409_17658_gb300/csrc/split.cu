@@ -506,6 +506,7 @@ struct SplitPass {
   int32_t max_slots;      // shared-memory rows = max_slots + 1 (row 0 is the dummy)
   int32_t max_list;       // list entries of one fiber at most
   int32_t slabs_per_cta;  // column slabs one CTA sweeps with its fiber staged once
+  int32_t fiber_x;        // 1: blockIdx.x is the fiber and blockIdx.y the slab group (the launch's choice)
   const int32_t* fstart;  // [fibers + 1] slot ranges: pass 1 into fmem, pass 2 X rows
   const int32_t* fmem;    // pass 1: p * 32 + w(p) per slot
   const int32_t* gls;     // [8 (fibers G) + 1] per (fiber, group): the 7 sub-list starts (even), then the end
@@ -631,7 +632,8 @@ __global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 4) split_pass_kerne
   in += a.in_col0;
   out += a.out_col0;
   const int lane = threadIdx.x % LR, gi = threadIdx.x / LR;
-  const int64_t f = blockIdx.y;
+  const int64_t f = a.fiber_x ? blockIdx.x : blockIdx.y;
+  const int64_t slab_group = a.fiber_x ? blockIdx.y : blockIdx.x;
   const uint4 inf4 = make_uint4(kInf2, kInf2, kInf2, kInf2);
 
   // stage the fiber's metadata once: sub-list bounds relative to the fiber's first list entry,
@@ -680,8 +682,8 @@ __global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 4) split_pass_kerne
   const uint32_t mu2 = (uint32_t)mu * 0x00010001u;
 
   const int64_t slabs = (a.ncols + W - 1) / W;
-  const int64_t sb_end = min(slabs, (int64_t)(blockIdx.x + 1) * a.slabs_per_cta);
-  for (int64_t sb = (int64_t)blockIdx.x * a.slabs_per_cta; sb < sb_end; ++sb) {
+  const int64_t sb_end = min(slabs, (slab_group + 1) * a.slabs_per_cta);
+  for (int64_t sb = slab_group * a.slabs_per_cta; sb < sb_end; ++sb) {
     const int64_t c = sb * W + lane * 8;
     const bool ok = c < a.ncols;
     __syncthreads();  // the metadata is staged / the previous slab has been consumed
@@ -923,7 +925,12 @@ cudaError_t launch_pass(const SplitPass& a, int W, int64_t fibers, cudaStream_t 
   bool staged = false;
   const size_t smem = pass_smem(a.max_slots, a.n_groups, a.max_list, W, FIRST, &staged);
   const int64_t slabs = (a.ncols + W - 1) / W;
-  const dim3 grid((unsigned)((slabs + a.slabs_per_cta - 1) / a.slabs_per_cta), (unsigned)fibers);
+  // Fibers along x, so that the CTAs resident on an SM belong to different fibers (different slot and
+  // list counts) and their staging and folding phases drift apart instead of running in step.
+  const int64_t groups = (slabs + a.slabs_per_cta - 1) / a.slabs_per_cta;
+  SplitPass b = a;
+  b.fiber_x = groups <= 65535 ? 1 : 0;
+  const dim3 grid = b.fiber_x ? dim3((unsigned)fibers, (unsigned)groups) : dim3((unsigned)groups, (unsigned)fibers);
   void (*k)(SplitPass) = nullptr;
   if (staged) {
     switch (W) {
@@ -940,7 +947,7 @@ cudaError_t launch_pass(const SplitPass& a, int W, int64_t fibers, cudaStream_t 
   }
   cudaError_t e = ensure_limits();
   if (e != cudaSuccess) return e;
-  k<<<grid, kSplitThreads, smem, s>>>(a);
+  k<<<grid, kSplitThreads, smem, s>>>(b);
   return cudaGetLastError();
 }
 
