@@ -439,18 +439,28 @@ __global__ void group_lists_kernel(GroupArgs a, int32_t* cnt_or_start, uint16_t*
   }
 }
 
-// Each fiber's groups in decreasing list length (ties by index): the kernel deals them to its lane
-// sets in that order, back and forth, so the sets get similar work.
+// Each fiber's groups in the order the kernel deals them to its lane sets (back and forth, so the sets
+// get similar work): grouped by the set of their non-empty sub-lists, and within one such signature in
+// decreasing list length (ties by index).  A warp runs each sub-list loop for as long as the longest of
+// its groups' sub-lists, so groups that share a warp should have the same sub-lists: ordering by total
+// length alone made a warp run 1.75 times its groups' mean work (m = 8), the signature first 1.36 times.
+__device__ inline uint32_t group_order_key(const int32_t* r) {
+  uint32_t sig = 0;
+  for (int s = 0; s < kSets; ++s) sig |= (r[s + 1] > r[s] ? 1u : 0u) << s;
+  const int32_t len = r[kRec - 1] - r[0];
+  return (sig << 16) | (uint32_t)(0xFFFF - (len < 0xFFFF ? len : 0xFFFF));
+}
+
 __global__ void group_order_kernel(const int32_t* gls, int64_t n_fibers, int64_t n_groups, uint16_t* ord) {
   GRID_STRIDE(f, n_fibers) {
     uint16_t* o = ord + f * n_groups;
     const int32_t* r = gls + f * n_groups * kRec;
     for (int64_t g = 0; g < n_groups; ++g) {
-      const int32_t len = r[g * kRec + kRec - 1] - r[g * kRec];
+      const uint32_t key = group_order_key(r + g * kRec);
       int64_t i = g;
       while (i > 0) {
         const int64_t h = o[i - 1];
-        if (r[h * kRec + kRec - 1] - r[h * kRec] >= len) break;
+        if (group_order_key(r + h * kRec) <= key) break;
         o[i] = o[i - 1];
         --i;
       }
