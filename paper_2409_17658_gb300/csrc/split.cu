@@ -524,7 +524,7 @@ struct SplitPass {
   const int32_t* gls;     // [8 (fibers G) + 1] per (fiber, group): the 7 sub-list starts (even), then the end
   const uint16_t* lst;    // 1-based slot numbers, 0 = dummy
   const int32_t* go;      // [(fibers G) * 4] output rows per boundary letter, or -1
-  const uint16_t* ord;    // [fibers G] each fiber's groups in decreasing list length
+  const uint16_t* ord;    // [fibers G] each fiber's groups in dealing order (group_order_kernel)
   int32_t* min_out;
   int32_t* diag_out;
   PowerState* st;  // ring mode: B = power slot k (pass 1), R = slot k + 1 (pass 2)
@@ -729,7 +729,7 @@ __global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 4) split_pass_kerne
     }
     __syncthreads();
 
-    // groups in decreasing work, dealt to the lane sets back and forth (0..G-1, G-1..0, ...)
+    // groups in the plan's order, dealt to the lane sets back and forth (0..G-1, G-1..0, ...)
     for (int round0 = 0; round0 < a.n_groups; round0 += G) {
       const int idx = round0 + (((round0 / G) & 1) ? (G - 1 - gi) : gi);
       if (idx >= a.n_groups) continue;
