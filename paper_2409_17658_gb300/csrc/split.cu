@@ -446,28 +446,35 @@ __global__ void group_lists_kernel(GroupArgs a, int32_t* cnt_or_start, uint16_t*
 // stay together too, so the back-and-forth dealing still balances the lane sets.  A model of the plans
 // (warp work over the groups' mean): m = 8 pass 2 1.39, m = 9 pass 2 1.20, against 1.76 and 1.70 for the
 // order by total length alone.
-__device__ inline bool group_before(const int32_t* ra, const int32_t* rb) {
+//
+// The order as one 64-bit key per group, smaller first: the seven sub-list lengths in the set order above,
+// each as 511 minus the length capped at 511 (9 bits), the first set in the top bits.  Lengths above 511
+// (only very unbalanced splits have such groups) tie, which only changes the order among them.
+__device__ inline uint64_t group_key(const int32_t* r) {
   const int order[kSets] = {4, 6, 2, 0, 1, 3, 5};  // set indexes of abc, acd, ac, a, c, bc, cd
+  uint64_t key = 0;
   for (int k = 0; k < kSets; ++k) {
     const int sidx = order[k];
-    const int32_t la = ra[sidx + 1] - ra[sidx], lb = rb[sidx + 1] - rb[sidx];
-    if (la != lb) return la > lb;
+    const int32_t len = r[sidx + 1] - r[sidx];
+    key = (key << 9) | (uint64_t)(511 - (len < 511 ? len : 511));
   }
-  return false;
+  return key;
 }
 
-__global__ void group_order_kernel(const int32_t* gls, int64_t n_fibers, int64_t n_groups, uint16_t* ord) {
-  GRID_STRIDE(f, n_fibers) {
-    uint16_t* o = ord + f * n_groups;
-    const int32_t* r = gls + f * n_groups * kRec;
-    for (int64_t g = 0; g < n_groups; ++g) {
-      int64_t i = g;
-      while (i > 0 && group_before(r + g * kRec, r + (int64_t)o[i - 1] * kRec)) {
-        o[i] = o[i - 1];
-        --i;
-      }
-      o[i] = (uint16_t)g;
-    }
+// One CTA per fiber: the groups' keys in shared memory, then each group's rank (the groups with a smaller
+// key, or an equal key and a smaller index) is its place in the order.
+__global__ void group_order_kernel(const int32_t* gls, int64_t n_groups, uint16_t* ord) {
+  extern __shared__ uint64_t keys[];
+  const int64_t f = blockIdx.x;
+  const int32_t* r = gls + f * n_groups * kRec;
+  for (int64_t g = threadIdx.x; g < n_groups; g += blockDim.x) keys[g] = group_key(r + g * kRec);
+  __syncthreads();
+  uint16_t* o = ord + f * n_groups;
+  for (int64_t g = threadIdx.x; g < n_groups; g += blockDim.x) {
+    const uint64_t kg = keys[g];
+    int64_t rank = 0;
+    for (int64_t h = 0; h < n_groups; ++h) rank += (keys[h] < kg || (keys[h] == kg && h < g)) ? 1 : 0;
+    o[rank] = (uint16_t)g;
   }
 }
 
@@ -1244,8 +1251,10 @@ extern "C" rd_status rd_split_plan(int m, int j, void* plan_dev, size_t plan_byt
   if (w1 == 0 || w2 == 0) return RD_ERR_ARG;  // a fiber does not fit in shared memory
   group_lists_kernel<true><<<grid_for(nrec1), 256, 0, s>>>(g1, at<int32_t>(P, L.gls1), at<uint16_t>(P, L.l1), nullptr);
   group_lists_kernel<true><<<grid_for(nrec2), 256, 0, s>>>(g2, at<int32_t>(P, L.gls2), at<uint16_t>(P, L.l2), nullptr);
-  group_order_kernel<<<grid_for(n_sigma), 64, 0, s>>>(at<int32_t>(P, L.gls1), n_sigma, L.nG1, at<uint16_t>(P, L.ord1));
-  group_order_kernel<<<grid_for(L.nPi), 64, 0, s>>>(at<int32_t>(P, L.gls2), L.nPi, L.nG2, at<uint16_t>(P, L.ord2));
+  group_order_kernel<<<(unsigned)n_sigma, 128, (size_t)L.nG1 * 8, s>>>(at<int32_t>(P, L.gls1), L.nG1,
+                                                                     at<uint16_t>(P, L.ord1));
+  group_order_kernel<<<(unsigned)L.nPi, 128, (size_t)L.nG2 * 8, s>>>(at<int32_t>(P, L.gls2), L.nG2,
+                                                                   at<uint16_t>(P, L.ord2));
   group_out_kernel<<<grid_for(nrec1), 256, 0, s>>>(g1, at<int32_t>(P, L.rankPi), at<int32_t>(P, L.xrank), n_sigma,
                                                    nullptr, 0, at<int32_t>(P, L.go1));
   group_out_kernel<<<grid_for(nrec2), 256, 0, s>>>(g2, at<int32_t>(P, L.rankPhi), nullptr, 0,
