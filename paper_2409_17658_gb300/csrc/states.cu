@@ -155,6 +155,15 @@ __global__ void __launch_bounds__(256) transfer_kernel(WordTable w, int64_t n, i
   const int tx = tid & 31, ty = tid >> 5;
   const int64_t pc = p0 + 8 * tx;
   if (pc >= lda) return;
+  // this thread's 8 destination words, read from shared memory once for all its rows (the lanes' words
+  // are 8 apart, so every such read is a bank-conflicted one)
+  Masks pj[8];
+  int16_t wj[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    pj[e] = pm[8 * tx + e];
+    wj[e] = pw[8 * tx + e];
+  }
   for (int r = ty; r < kTq; r += 8) {
     const int64_t q = q0 + r;
     if (q >= n) break;
@@ -166,9 +175,10 @@ __global__ void __launch_bounds__(256) transfer_kernel(WordTable w, int64_t n, i
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int j = 8 * tx + e + h;
-        const bool arc = (p0 + j < n) && can_follow(qf, pm[j], full);
-        int label = pw[j];
-        if (LOSS) label = 10 * __popc(pm[j].a) + 5 * __popc(pm[j].b) - 2 * newly_dominated(qm[r], pm[j]) + 2 * w.m;
+        const bool arc = (p0 + j < n) && can_follow(qf, pj[e + h], full);
+        int label = wj[e + h];
+        if (LOSS)
+          label = 10 * __popc(pj[e + h].a) + 5 * __popc(pj[e + h].b) - 2 * newly_dominated(qm[r], pj[e + h]) + 2 * w.m;
         v[h] = arc ? (int16_t)label : kInf;
       }
       packed[e / 2] = (uint32_t)(uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
