@@ -67,6 +67,8 @@ def _load():
             lib.rdo_power_until_periodic.restype = ctypes.c_int
             lib.rdo_power_rows.argtypes = [ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp]
             lib.rdo_power_rows.restype = ctypes.c_int
+            lib.rdo_power_until_periodic_rows.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp]
+            lib.rdo_power_until_periodic_rows.restype = ctypes.c_int
             lib.rdo_brute_force.argtypes = [ctypes.c_int, ctypes.c_int]
             lib.rdo_brute_force.restype = i64
             lib.rdo_row_dp.argtypes = [ctypes.c_int, ctypes.c_int]
@@ -204,6 +206,24 @@ def power_until_periodic(m: int = 0, a: np.ndarray | None = None, kmax: int = 64
     jj = int(j[0])
     return dict(found=(rc == 0), k=int(k[0]) if rc == 0 else None, p=int(p[0]) if rc == 0 else None,
                 q=int(q[0]) if rc == 0 else None, j=jj, gamma=gamma[: jj + 1].copy())
+
+
+def power_until_periodic_rows(m: int, kmax: int = 40) -> dict:
+    """Algorithm 2 with the first-repeat rule, streamed one start word at a time (no dense power kept).
+
+    Same rule and results as power_until_periodic(m); gamma is filled for k = 1..kmax whether or
+    not a repeat was found (index 0 unused), and j is the repeat's j (kmax when none).
+    """
+    gamma = np.zeros(kmax + 1, dtype=np.int64)
+    k = np.zeros(1, dtype=np.int32)
+    p = np.zeros(1, dtype=np.int32)
+    q = np.zeros(1, dtype=np.int64)
+    j = np.zeros(1, dtype=np.int32)
+    rc = _load().rdo_power_until_periodic_rows(m, kmax, _ptr(gamma), _ptr(k), _ptr(p), _ptr(q), _ptr(j))
+    if rc not in (0, 5):
+        raise RuntimeError(f"oracle power_until_periodic_rows failed rc={rc}")
+    return dict(found=(rc == 0), k=int(k[0]) if rc == 0 else None, p=int(p[0]) if rc == 0 else None,
+                q=int(q[0]) if rc == 0 else None, j=int(j[0]), gamma=gamma)
 
 
 def power_rows(m: int, rows, kmax: int) -> np.ndarray:

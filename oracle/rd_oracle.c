@@ -391,6 +391,136 @@ int rdo_power_rows(int m, const int64_t *rows, int nrows, int kmax, int64_t *out
 }
 
 /*
+ * Algorithm 2 with the first-repeat rule (Lemma 2, Prop. 7), one start word at a
+ * time, so that no power is ever held whole (m = 9 has N = 21909; one dense power
+ * in int64 is 3.8 GB and the search needs 27 of them).
+ *
+ * Row p of A^k is e_p (x) A^k: by Theorem 1 its entry t is the least label of a
+ * k-arc walk from word p to word t.  For each p the rows k = 1..kmax are built by
+ * extending every walk by one arc (arcs from the Sec. 4.A rules, label = weight of
+ * the destination word).  Then, for that row alone:
+ *   - gamma[k] = min over p of (A^k)_pp (Corollary 6) takes the diagonal entry;
+ *   - for every pair i < j <= kmax, "row p of A^j = beta + row p of A^i" is tested
+ *     (same infinite entries, one constant difference on the finite ones).
+ * A^j = beta (x) A^i holds for the matrix iff it holds for every row with one
+ * common beta, so each pair keeps one flag and the beta of the first row that has
+ * a finite entry.  The answer is the smallest j with a surviving pair (i, j),
+ * reported as (k, p, q) = (i, j - i, beta) -- the same rule and the same results
+ * as rdo_power_until_periodic.  gamma[1..kmax] are all filled; j_out is the j of
+ * the repeat, or kmax when none was found (return 5).  Memory: kmax * N int64 per
+ * thread.
+ */
+int rdo_power_until_periodic_rows(int m, int kmax, int64_t *gamma, int32_t *k_out, int32_t *p_out, int64_t *q_out,
+                                  int32_t *j_out) {
+  int64_t N = rdo_num_words(m);
+  if (N <= 0 || kmax < 2 || kmax > 200) return 1;
+  uint32_t *code = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N);
+  int32_t *wt = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+  if (!code || !wt) { free(code); free(wt); return 2; }
+  rdo_words(m, code, wt, N);
+  int64_t *ptr = 0, *col = 0, *w = 0;
+  if (build_arcs_from_rules(m, N, code, wt, &ptr, &col, &w)) {
+    free(code); free(wt); free(ptr); free(col); free(w);
+    return 2;
+  }
+  /* pair (i, j), 1 <= i < j <= kmax, is slot (j-1)(j-2)/2 + (i-1) */
+  const int npairs = kmax * (kmax - 1) / 2;
+  int64_t *gmin = (int64_t *)malloc(sizeof(int64_t) * (size_t)(kmax + 1));
+  int *alive = (int *)malloc(sizeof(int) * (size_t)npairs);
+  int *have = (int *)malloc(sizeof(int) * (size_t)npairs);
+  int64_t *beta = (int64_t *)malloc(sizeof(int64_t) * (size_t)npairs);
+  int rc = 0;
+  if (!gmin || !alive || !have || !beta) rc = 2;
+  if (rc == 0) {
+    for (int k = 0; k <= kmax; ++k) gmin[k] = RDO_INF;
+    for (int s = 0; s < npairs; ++s) { alive[s] = 1; have[s] = 0; beta[s] = 0; }
+#pragma omp parallel
+    {
+      int64_t *rows = (int64_t *)malloc(sizeof(int64_t) * (size_t)kmax * (size_t)N); /* row of A^k at (k-1)*N */
+      int64_t *lmin = (int64_t *)malloc(sizeof(int64_t) * (size_t)(kmax + 1));
+      int *lalive = (int *)malloc(sizeof(int) * (size_t)npairs);
+      int *lhave = (int *)malloc(sizeof(int) * (size_t)npairs);
+      int64_t *lbeta = (int64_t *)malloc(sizeof(int64_t) * (size_t)npairs);
+      int ok = rows && lmin && lalive && lhave && lbeta;
+      if (ok) {
+        for (int k = 0; k <= kmax; ++k) lmin[k] = RDO_INF;
+        for (int s = 0; s < npairs; ++s) { lalive[s] = 1; lhave[s] = 0; lbeta[s] = 0; }
+      }
+#pragma omp for schedule(dynamic, 8)
+      for (int64_t p = 0; p < N; ++p) {
+        if (!ok) continue;
+        int64_t *cur = rows; /* k = 1: row p of A */
+        for (int64_t t = 0; t < N; ++t) cur[t] = RDO_INF;
+        for (int64_t e = ptr[p]; e < ptr[p + 1]; ++e) cur[col[e]] = w[e];
+        for (int k = 2; k <= kmax; ++k) {
+          const int64_t *prev = rows + (size_t)(k - 2) * N;
+          int64_t *nxt = rows + (size_t)(k - 1) * N;
+          for (int64_t t = 0; t < N; ++t) nxt[t] = RDO_INF;
+          for (int64_t t = 0; t < N; ++t) {
+            if (prev[t] == RDO_INF) continue;
+            for (int64_t e = ptr[t]; e < ptr[t + 1]; ++e) {
+              int64_t v = prev[t] + w[e];
+              if (v < nxt[col[e]]) nxt[col[e]] = v;
+            }
+          }
+        }
+        for (int k = 1; k <= kmax; ++k) {
+          int64_t d = rows[(size_t)(k - 1) * N + p];
+          if (d < lmin[k]) lmin[k] = d;
+        }
+        for (int j = 2; j <= kmax; ++j)
+          for (int i = 1; i < j; ++i) {
+            const int s = (j - 1) * (j - 2) / 2 + (i - 1);
+            if (!lalive[s]) continue;
+            int64_t b;
+            if (!same_up_to_offset(rows + (size_t)(i - 1) * N, rows + (size_t)(j - 1) * N, N, &b)) {
+              lalive[s] = 0;
+              continue;
+            }
+            int row_has_finite = 0;
+            for (int64_t t = 0; t < N && !row_has_finite; ++t) row_has_finite = (rows[(size_t)(i - 1) * N + t] != RDO_INF);
+            if (!row_has_finite) continue; /* an all-infinite row fixes no beta */
+            if (!lhave[s]) { lhave[s] = 1; lbeta[s] = b; }
+            else if (lbeta[s] != b) lalive[s] = 0;
+          }
+      }
+#pragma omp critical
+      {
+        if (!ok) rc = 2;
+        else {
+          for (int k = 1; k <= kmax; ++k)
+            if (lmin[k] < gmin[k]) gmin[k] = lmin[k];
+          for (int s = 0; s < npairs; ++s) {
+            if (!lalive[s]) { alive[s] = 0; continue; }
+            if (!lhave[s]) continue;
+            if (!have[s]) { have[s] = 1; beta[s] = lbeta[s]; }
+            else if (beta[s] != lbeta[s]) alive[s] = 0;
+          }
+        }
+      }
+      free(rows); free(lmin); free(lalive); free(lhave); free(lbeta);
+    }
+  }
+  if (rc == 0) {
+    rc = 5;
+    for (int k = 1; k <= kmax; ++k) gamma[k] = gmin[k];
+    *j_out = kmax;
+    for (int j = 2; j <= kmax && rc == 5; ++j)
+      for (int i = 1; i < j; ++i) {
+        const int s = (j - 1) * (j - 2) / 2 + (i - 1);
+        if (alive[s]) {
+          *k_out = i; *p_out = j - i; *q_out = have[s] ? beta[s] : 0; *j_out = j;
+          rc = 0;
+          break;
+        }
+      }
+  }
+  free(code); free(wt); free(ptr); free(col); free(w);
+  free(gmin); free(alive); free(have); free(beta);
+  return rc;
+}
+
+/*
  * Brute force from the definition (Sec. 1): gamma_R(G) is the least weight
  * sum f(v) over f: V -> {0,1,2} such that every v with f(v) = 0 has a neighbour w
  * with f(w) = 2.  G = P_m box C_n: vertex (r, c), r = 0..m-1 along the path, c =

@@ -7,11 +7,12 @@ a swapped operand or a wrong rule in the oracle fails at least one of them.
 """
 import itertools
 import math
+import os
 
 import numpy as np
 import pytest
 
-from conftest import read_golden
+from conftest import oracle_m9, read_golden
 
 INF = 0x3FFFFFFFFFFFFFFF
 LETTERS = "abcd"
@@ -257,6 +258,59 @@ def test_period_m8_matches_table2(orc):
     assert g[3] == 13  # the printed closed form gives 12 at n = 3 (erratum)
     for n in range(4, r["j"] + 1):
         assert g[n] == _paper_m8(n), f"n={n}"
+
+
+# ---------------------------------------------------------------- the row-streamed search (m = 9)
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5, 6, 7])
+def test_streamed_search_equals_dense_search(orc, m):
+    d = orc.power_until_periodic(m, kmax=40)
+    s = orc.power_until_periodic_rows(m, kmax=30)
+    assert s["found"] and (s["k"], s["p"], s["q"], s["j"]) == (d["k"], d["p"], d["q"], d["j"])
+    assert np.array_equal(s["gamma"][1:d["j"] + 1], d["gamma"][1:d["j"] + 1])
+    # past the repeat the streamed gamma keeps following Prop. 7
+    for n in range(d["j"] + 1, 31):
+        assert s["gamma"][n] == orc.gamma_from_period(d["gamma"], d["k"], d["p"], d["q"], n), (m, n)
+
+
+def test_streamed_search_not_found_within_kmax(orc):
+    d = orc.power_until_periodic(3, kmax=40)
+    assert d["j"] == 15  # m = 3: A^15 = 6 (x) A^11 is the first repeat
+    s = orc.power_until_periodic_rows(3, kmax=14)
+    assert not s["found"] and s["j"] == 14
+    assert np.array_equal(s["gamma"][1:15], d["gamma"][1:15])
+
+
+@pytest.mark.slow
+def test_streamed_search_m8_matches_table2(orc):
+    s = orc.power_until_periodic_rows(8, kmax=28)
+    assert s["found"] and (s["k"], s["p"], s["q"]) == (21, 5, 18)
+    g = s["gamma"]
+    assert g[3] == 13  # erratum of the printed m = 8 form at n = 3
+    for n in range(4, 29):
+        assert g[n] == _paper_m8(n), f"n={n}"
+
+
+def test_oracle_m9_golden_against_the_paper(orc):
+    """The stored m = 9 result of the oracle against what the paper prints: Table 2's m = 9 row, the m = 9
+    closed form of Sec. 4.C for every n = 3..k + p, and the path DP for small n."""
+    o = oracle_m9()
+    table = {int(r[0]): tuple(map(int, r[1:])) for r in read_golden("paper_table2_periods.txt")}
+    assert (o["k"], o["p"], o["q"]) == table[9]
+    assert o["j"] == o["k"] + o["p"]
+    for n in range(3, o["j"] + 1):
+        assert o["gamma"][n] == _paper_m9(n), n
+    for n in range(3, 6):
+        assert o["gamma"][n] == orc.row_dp(9, n), n
+
+
+@pytest.mark.skipif(not os.environ.get("RD_ORACLE_M9"), reason="about 5 minutes on 8 cores; set RD_ORACLE_M9=1")
+def test_oracle_m9_golden_regenerates(orc):
+    """The stored m = 9 values are the oracle's: the row-streamed search run again gives the same file."""
+    o = oracle_m9()
+    s = orc.power_until_periodic_rows(9, kmax=len(o["gamma"]) - 1)
+    assert s["found"] and (s["k"], s["p"], s["q"], s["j"]) == (o["k"], o["p"], o["q"], o["j"])
+    assert [int(x) for x in s["gamma"][1:]] == o["gamma"][1:]
 
 
 def test_lemma2_holds_beyond_the_repeat(orc):
