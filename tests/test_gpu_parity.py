@@ -9,7 +9,7 @@ import math
 import numpy as np
 import pytest
 
-from conftest import read_golden
+from conftest import oracle_m9, read_golden
 
 pytestmark = pytest.mark.gpu
 
@@ -114,6 +114,49 @@ def test_minplus_gemm(rd, torch_mod, orc, shape, dist):
     assert mn.item() == want.min()
 
 
+@pytest.mark.parametrize("shape", [(1, 300, 1000), (70, 90, 130), (257, 1000, 511), (1030, 129, 2000)])
+def test_minplus_gemm_host(rd, torch_mod, orc, shape):
+    """The product through the host-buffer entry point: host strides wider than the rows, pinned and
+    pageable buffers, two streams in turn with their own staging buffers; element by element."""
+    torch = torch_mod
+    from paper_2409_17658_gb300 import inputs
+
+    M, K, N = shape
+    a = inputs.matrix(M, K, seed=81, dist="wide")
+    b = inputs.matrix(K, N, seed=82, dist="wide")
+    want = orc.minplus_i16(a, b)
+    a_wide = np.full((M, K + 5), -1, dtype=np.int16)
+    a_wide[:, :K] = a
+    b_wide = np.full((K, N + 3), -1, dtype=np.int16)
+    b_wide[:, :N] = b
+    wbytes = rd.minplus_gemm_host_work_bytes(M, N, K)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    works = [torch.empty(wbytes, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    mins = [torch.zeros(1, dtype=torch.int32, device="cuda") for _ in range(2)]
+    pinned = [torch.from_numpy(a_wide).pin_memory()[:, :K], torch.from_numpy(b_wide).pin_memory()[:, :N]]
+    outs = [torch.full((M, N + 1), 123, dtype=torch.int16).pin_memory()[:, :N] for _ in range(2)]
+    for i in range(2):  # pinned, two streams in turn
+        rd.minplus_gemm_host(pinned[0], pinned[1], outs[i], works[i], min_out=mins[i], stream=streams[i])
+    c_np = np.full((M, N + 2), 321, dtype=np.int16)
+    rd.minplus_gemm_host(a_wide[:, :K], b_wide[:, :N], c_np[:, :N], works[0], stream=streams[0])  # pageable
+    torch.cuda.synchronize()
+    for i in range(2):
+        assert np.array_equal(outs[i].numpy().astype(np.int32), want), i
+        assert mins[i].item() == want.min()
+    assert np.array_equal(c_np[:, :N].astype(np.int32), want)
+    assert np.all(c_np[:, N:] == 321)
+
+
+def test_minplus_gemm_host_rejects_short_work(rd, torch_mod):
+    torch = torch_mod
+    a = np.zeros((16, 16), dtype=np.int16)
+    c = np.zeros((16, 16), dtype=np.int16)
+    work = torch.empty(rd.minplus_gemm_host_work_bytes(16, 16, 16) - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(rd.RdError) as e:
+        rd.minplus_gemm_host(a, a, c, work)
+    assert e.value.status == rd.RD_ERR_NOMEM
+
+
 def test_minplus_gemm_k0_and_empty(rd, torch_mod):
     torch = torch_mod
     A = torch.zeros((5, 8), dtype=torch.int16, device="cuda")
@@ -206,12 +249,16 @@ def test_power_m8_matches_oracle(rd, torch_mod, orc):
 
 
 def test_power_m9_full_size(rd, torch_mod, orc):
-    """m = 9 (N = 21909): Table 2's triple, the row DP for n <= 7, and sampled rows of the resident powers."""
+    """m = 9 (N = 21909): the oracle's first repeat and gamma[1..j] (its row-streamed search), Table 2's
+    triple, the row DP for n <= 7, and sampled rows of the resident powers."""
     A, n = rd.transfer_matrix(9)
     slots = 8
     r, work = run_power(rd, torch_mod, A, n, kmax=40, slots=slots)
     table = {int(x[0]): tuple(map(int, x[1:])) for x in read_golden("paper_table2_periods.txt")}
     assert r["found"] and (r["k"], r["p"], r["q"]) == table[9]
+    o = oracle_m9()
+    assert (r["k"], r["p"], r["q"], r["j"]) == (o["k"], o["p"], o["q"], o["j"])
+    assert [int(x) for x in r["gamma"][1:r["j"] + 1]] == o["gamma"][1:o["j"] + 1]
     g = r["gamma"]
     for nn in range(3, 8):
         assert g[nn] == orc.row_dp(9, nn)
@@ -283,6 +330,20 @@ def test_gamma_R_matches_algorithm1(rd, orc):
         assert rd.gamma_R(1, n) == math.ceil(2 * n / 3)
 
 
+def test_gamma_R_m9_closed_form(rd):
+    """rd_gamma_R(9, n) against the oracle's gamma for n < k + p and, beyond, the solution of Prop. 7 from the
+    oracle's first repeat; and against the m = 9 closed form printed in Sec. 4.C (4n if 5 | n, else 4n + 2)."""
+    o = oracle_m9()
+    for n in range(3, 501):
+        if n < o["k"] + o["p"]:
+            want = o["gamma"][n]
+        else:
+            want = o["gamma"][o["k"] + (n - o["k"]) % o["p"]] + o["q"] * ((n - o["k"]) // o["p"])
+        got = rd.gamma_R(9, n)
+        assert got == want, n
+        assert got == (4 * n if n % 5 == 0 else 4 * n + 2), n
+
+
 def test_gamma_R_closed_forms_m7(rd):
     for n in range(3, 120):
         want = 20 if n == 6 else math.ceil(16 * n / 5) + (0 if n % 5 == 0 else 1)
@@ -339,7 +400,9 @@ def test_power_sparse_m9_equals_dense(rd, torch_mod, orc, R):
     plan = rd.sparse_plan(A, n, n, R)
     work = rd.power_workspace(n, A.stride(0), 40, 8)
     r = rd.power_until_periodic_sparse(A, n, plan, 40, work)
-    assert (r["k"], r["p"], r["q"]) == (22, 5, 20)
+    o = oracle_m9()
+    assert (r["k"], r["p"], r["q"], r["j"]) == (o["k"], o["p"], o["q"], o["j"]) == (22, 5, 20, 27)
+    assert [int(x) for x in r["gamma"][1:r["j"] + 1]] == o["gamma"][1:o["j"] + 1]
     for nn in range(3, 8):
         assert r["gamma"][nn] == orc.row_dp(9, nn)
     # same gamma sequence as the dense step
@@ -522,6 +585,48 @@ def test_sparse_minplus_tma(rd, torch_mod, orc, shape, R):
     assert np.array_equal(got[:, :N].astype(np.int32), want)
     assert np.all(got[:, N:] == 777)
     assert mn.item() == want.min()
+
+
+@pytest.mark.parametrize("R", [1, 8])
+def test_sparse_minplus_tma_wait_runs_out(rd, torch_mod, orc, R):
+    """The bulk-copy kernel's bounded wait gives up and says so, and the GPU stays usable.  Every CTA's
+    producer stops before entry 3 of its block, as a lost copy would; the consumers wait for that entry,
+    give up after 4096 try_wait rounds with no copy in flight, and report the timeout bit (8).  The next
+    call, with the default limit and no stop, is bit-exact against the oracle."""
+    torch = torch_mod
+    from paper_2409_17658_gb300 import inputs
+
+    M, K, N = 130, 200, 1030
+    a = inputs.matrix(M, K, seed=71, dist="wide")
+    keep = inputs.matrix(M, K, seed=73, dist="u32") < 6
+    a = np.where(keep, a, I16_INF).astype(np.int16)
+    b = inputs.matrix(K, N, seed=72, dist="wide")
+    A = upload(torch, a)
+    B = upload(torch, b)
+    plan = rd.sparse_plan(A, M, K, R)
+    starts = plan["block_start"].cpu().numpy()
+    assert (np.diff(starts) > 3).any()  # some blocks need the withheld entry
+    C = torch.full((M, (N + 7) // 8 * 8), 777, dtype=torch.int16, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rd.sparse_minplus_tma_bounded(plan, B, C, err, wait_limit=4096, stop_at=3, N=N)
+    torch.cuda.synchronize()
+    assert err.item() == 8
+    err.zero_()
+    rd.sparse_minplus_tma_bounded(plan, B, C, err, wait_limit=1 << 20, stop_at=-1, N=N)
+    assert err.item() == 0
+    assert np.array_equal(C.cpu().numpy()[:, :N].astype(np.int32), orc.minplus_i16(a, b))
+
+
+def test_sparse_minplus_tma_bounded_rejects_bad_knobs(rd, torch_mod):
+    lib = rd._lib()
+    import ctypes
+
+    vp = ctypes.c_void_p
+    err = torch_mod.zeros(1, dtype=torch_mod.int32, device="cuda")
+    e = vp(err.data_ptr())
+    assert lib.rd_sparse_minplus_tma_bounded(1, 0, None, None, None, 8, 0, None, 8, None, e, 0, -1, None) == rd.RD_ERR_ARG
+    assert lib.rd_sparse_minplus_tma_bounded(1, 0, None, None, None, 8, 0, None, 8, None, e, 16, -2, None) == rd.RD_ERR_ARG
+    assert lib.rd_sparse_minplus_tma_bounded(1, 0, None, None, None, 8, 0, None, 8, None, e, 16, -1, None) == rd.RD_OK
 
 
 # ---------------------------------------------------------------- vector x matrix (one row against an N x N operand)

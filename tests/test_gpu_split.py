@@ -8,7 +8,7 @@ period search; seeded operands come from paper_2409_17658_gb300.inputs.
 import numpy as np
 import pytest
 
-from conftest import read_golden
+from conftest import oracle_m9, read_golden
 
 pytestmark = pytest.mark.gpu
 
@@ -209,8 +209,9 @@ def test_power_split_m8_matches_oracle(rd, torch_mod, orc):
 
 
 def test_power_split_m9(rd, torch_mod, orc):
-    """m = 9 (N = 21909): Table 2's triple, the path DP for n <= 7, sampled rows of the resident powers
-    against the oracle, and the same gamma sequence and final power as the sparse step."""
+    """m = 9 (N = 21909): the oracle's first repeat and gamma[1..j], Table 2's triple, the path DP for n <= 7,
+    sampled rows of the resident powers against the oracle, and the same gamma sequence and final power as
+    the sparse step."""
     torch = torch_mod
     m, kmax, slots = 9, 40, 8
     A, n = rd.transfer_matrix(m)
@@ -220,6 +221,9 @@ def test_power_split_m9(rd, torch_mod, orc):
     r = rd.power_until_periodic_split(A, plan, kmax, work)
     table = {int(x[0]): tuple(map(int, x[1:])) for x in read_golden("paper_table2_periods.txt")}
     assert r["found"] and (r["k"], r["p"], r["q"]) == table[9]
+    o = oracle_m9()  # the oracle's row-streamed first-repeat search
+    assert (r["k"], r["p"], r["q"], r["j"]) == (o["k"], o["p"], o["q"], o["j"])
+    assert [int(x) for x in r["gamma"][1:r["j"] + 1]] == o["gamma"][1:o["j"] + 1]
     for nn in range(3, 8):
         assert r["gamma"][nn] == orc.row_dp(m, nn)
     rng = np.random.default_rng(909)
