@@ -34,12 +34,13 @@ sys.path.insert(0, ROOT)
 
 N_HEAD = 16384
 SEED_A, SEED_B = 1, 2
-# DPX peak derived from unit counts and clock: 152 SMs x 64 __viaddmin_s16x2 lanes per clock
-# (measured 126.6 add-mins/clock/SM in a register-resident loop) x 2 add-mins per lane x 2070 MHz.
+# Nominal DPX rate from unit counts and clock: 152 SMs x 64 __viaddmin_s16x2 lanes per clock x 2 add-mins per
+# lane x 2070 MHz.  The roofline's peak is the measured one (rd_measure_addmin_peak, run by this script before
+# the timed region); the nominal figure is printed beside it.
 SMS, DPX_LANES_PER_CLK, ADDMIN_PER_LANE, SM_MAX_MHZ = 152, 64, 2, 2070.0
 PEAK_GOPS = SMS * DPX_LANES_PER_CLK * ADDMIN_PER_LANE * SM_MAX_MHZ * 1e6 / 1e9
-# DRAM bytes (read + write) per launch of the product kernel at N = 16384, from the one-pass ncu
-# capture summarised in profiles/minplus_gemm_n16384_dram.md (8.60 GB read + 0.552 GB written).
+# DRAM bytes (read + write) per launch of the product kernel at N = 16384, from a one-pass ncu capture of
+# dram__bytes_read.sum and dram__bytes_write.sum on that launch (8.60 GB read + 0.552 GB written).
 GEMM_TRAFFIC_BYTES = 9.152e9
 CONFIG_NAME = "synthetic dense (min,+) GEMM N=16384, int16 uniform[0,32], P(inf)=0.5"
 HBM_GBS = 6652.3  # measured copy bandwidth of the GB300s (STREAM-style, read + write)
@@ -652,6 +653,10 @@ def main() -> None:
     for _ in range(max(args.warmup, 3)):
         rd.minplus_gemm(A, B, C, min_out=mn)
     torch.cuda.synchronize()
+    # the roofline's denominator, measured on this GPU (a 17 ms register-resident DPX loop)
+    with ClockSampler(local) as peak_clocks:
+        peak = rd.measure_addmin_peak(trips=8192)
+    peak["clocks"] = peak_clocks.summary()
 
     # ---- device-resident timed region: events around every launch
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -681,50 +686,40 @@ def main() -> None:
     a = A.cpu().numpy()
     b = B.cpu().numpy()
 
-    # ---- end to end through the C ABI with host buffers.  Every step copies its operands in from
-    # pinned host memory and its result back out; two buffer sets and two copy streams overlap the
-    # copies of one step with the product of another.
+    # ---- end to end through the C ABI with host buffers: every step is one rd_minplus_gemm_host call,
+    # which copies A and B in from pinned host memory, runs the product and copies C back out.  Steps
+    # alternate between two streams with their own staging buffers, so one step's copies overlap the
+    # neighbouring step's product.
+    del C
     a_pin = torch.from_numpy(a).pin_memory()
     b_pin = torch.from_numpy(b).pin_memory()
     c_pin = [torch.empty((n, n), dtype=torch.int16).pin_memory() for _ in range(2)]
-    bufs = [(A, B, C)] + [tuple(torch.empty_like(A) for _ in range(3))]
-    h2d_s, d2h_s = torch.cuda.Stream(), torch.cuda.Stream()
-    ev = lambda: torch.cuda.Event()  # noqa: E731
-    h2d_done, comp_done, d2h_done = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+    wbytes = rd.minplus_gemm_host_work_bytes(n, n, n)
+    works = [torch.empty(wbytes, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    e2e_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
     e2e_steps = max(2, min(args.steps, 6))
+    for i in range(2):  # warm-up of both streams and staging buffers
+        rd.minplus_gemm_host(a_pin, b_pin, c_pin[i], works[i], stream=e2e_streams[i])
     barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    h2d_s.wait_event(e0)
+    for st_ in e2e_streams:
+        st_.wait_stream(stream)
     for i in range(e2e_steps):
-        k = i % 2
-        Ak, Bk, Ck = bufs[k]
-        with torch.cuda.stream(h2d_s):
-            if i >= 2:
-                h2d_s.wait_event(comp_done[k])  # the product two steps back has read this set
-            Ak.copy_(a_pin, non_blocking=True)
-            Bk.copy_(b_pin, non_blocking=True)
-            h2d_done[k].record(h2d_s)
-        stream.wait_event(h2d_done[k])
-        if i >= 2:
-            stream.wait_event(d2h_done[k])  # the result two steps back has left this set
-        rd.minplus_gemm(Ak, Bk, Ck, min_out=mn)
-        comp_done[k].record(stream)
-        with torch.cuda.stream(d2h_s):
-            d2h_s.wait_event(comp_done[k])
-            c_pin[k].copy_(Ck, non_blocking=True)
-            d2h_done[k].record(d2h_s)
-    stream.wait_event(d2h_done[(e2e_steps - 1) % 2])
-    stream.wait_event(d2h_done[(e2e_steps - 2) % 2])
+        rd.minplus_gemm_host(a_pin, b_pin, c_pin[i % 2], works[i % 2], stream=e2e_streams[i % 2])
+    for st_ in e2e_streams:
+        stream.wait_stream(st_)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     e2e_value = job_throughput(world, e2e_steps, ops_per_step, e2e_ms)
-    assert np.array_equal(c_pin[0][:2].numpy(), C[:2].cpu().numpy())
-    del bufs
+    C_check = torch.empty((2, n), dtype=torch.int16, device="cuda")
+    rd.minplus_gemm(A[:2], B, C_check)
+    assert np.array_equal(c_pin[0][:2].numpy(), C_check.cpu().numpy())
+    del works, C_check
 
     extra = {}
     if rank == 0:
@@ -745,24 +740,33 @@ def main() -> None:
 
     if rank == 0:
         achieved = ops_per_step / (per_launch_ms * 1e-3) / 1e9
-        roof = {"bound": "alu", "achieved": achieved, "peak": PEAK_GOPS, "unit": "G add-min/s",
-                "frac": achieved / PEAK_GOPS, "traffic": GEMM_TRAFFIC_BYTES,
+        per_clk = peak["addmin_per_clk_per_sm"]
+        peak_max = per_clk * peak["sm_count"] * SM_MAX_MHZ * 1e6 / 1e9  # measured rate per clock at the max clock
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "G add-min/s",
+                "frac": achieved / peak_max, "traffic": GEMM_TRAFFIC_BYTES,
                 "kernel": "minplus_gemm_kernel<false>", "per_launch_ms": per_launch_ms,
-                "peak_basis": "152 SMs x 64 DPX s16x2 lanes/clk x 2 add-min x 2070 MHz (derived; microbenchmark "
-                              "measured 126.6 add-min/clk/SM)"}
+                "peak_basis": "measured",
+                "peak_how": (f"rd_measure_addmin_peak: {per_clk:.2f} add-min/clk/SM (clock64 spans of a full wave "
+                             f"of __viaddmin_s16x2 chains) x {peak['sm_count']} SMs x {SM_MAX_MHZ:.0f} MHz"),
+                "peak_measured_run": {"addmin_per_clk_per_sm": per_clk, "gops_at_run_clock": peak["addmin_per_s"] / 1e9,
+                                      "run_sm_mhz": peak["sm_mhz"], "ms": peak["ms"], "clocks": peak["clocks"]},
+                "peak_nominal": PEAK_GOPS,
+                "peak_nominal_formula": "152 SMs x 64 DPX s16x2 lanes/clk x 2 add-min x 2070 MHz",
+                "frac_of_nominal": achieved / PEAK_GOPS}
         if clk.get("sm_mhz"):
-            roof["frac_at_sampled_clock"] = achieved / (PEAK_GOPS * clk["sm_mhz"] / SM_MAX_MHZ)
+            roof["frac_at_sampled_clock"] = achieved / (per_clk * peak["sm_count"] * clk["sm_mhz"] * 1e6 / 1e9)
         line = {"metric": "(min,+) add-min GOPS and % of GB300 DPX/INT peak at N=16384; gamma_R time-to-period vs oracle",
                 "value": value, "unit": "G add-min/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "int16", "data": "synthetic",
                 "config": {"workload": CONFIG_NAME, "N": n, "seeds": [SEED_A, SEED_B], "parallelism": f"replicas{world}",
                            "l2": "operands 2 x 512 MiB > 129 MB L2; no flush"},
-                "frac_of_peak": value / world / PEAK_GOPS,
+                "frac_of_peak": value / world / peak_max,
                 "e2e": {"value": e2e_value, "unit": "G add-min/s", "h2d_bytes_per_step": 2 * a.nbytes,
                         "d2h_bytes_per_step": a.nbytes, "steps": e2e_steps,
-                        "how": "pinned host operands in, result out, every step; copies overlapped with the "
-                               "product of the neighbouring step (two buffer sets, two copy streams)"},
+                        "how": "one rd_minplus_gemm_host call per step (pinned host A, B in; C out); steps "
+                               "alternate two streams and staging buffers, so copies overlap the neighbouring "
+                               "step's product"},
                 "gpu_launches": 2 * args.steps,
                 "roofline": roof, "clocks": clk}
         line.update(extra)

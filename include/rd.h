@@ -122,6 +122,26 @@ rd_status rd_minplus_gemm(const int16_t *A, int64_t lda, const int16_t *B, int64
                           int64_t M, int64_t N, int64_t K, int32_t *min_out, cudaStream_t s);
 
 /*
+ * rd_minplus_gemm_host -- rd_minplus_gemm (Sec. 3's product) for operands in
+ * host memory: A (M x K, row stride lda elements) and B (K x N, ldb) are read
+ * from host memory and C (M x N, ldc) is written to host memory.  Host strides
+ * need only be >= the row length; host pointers have no alignment rule.  The
+ * operands are staged in the caller's device buffer work_dev (256-byte aligned,
+ * >= rd_minplus_gemm_host_work_bytes(M, N, K)): enqueued on s are the copies of
+ * A and B in, the product (min_out as in rd_minplus_gemm), and the copy of C
+ * out.  Asynchronous: the host buffers must stay valid and C must not be read
+ * until s has passed this call.  With page-locked (pinned) host buffers the
+ * copies run as DMA beside other streams' work, so a caller that alternates two
+ * streams and two staging buffers overlaps one product's copies with another's
+ * arithmetic; with pageable buffers CUDA stages the copies and may block.
+ * RD_ERR_ARG for bad sizes or pointers, RD_ERR_NOMEM for a short work buffer.
+ */
+rd_status rd_minplus_gemm_host_work_bytes(int64_t M, int64_t N, int64_t K, size_t *bytes);
+rd_status rd_minplus_gemm_host(const int16_t *A_host, int64_t lda, const int16_t *B_host, int64_t ldb, int16_t *C_host,
+                               int64_t ldc, int64_t M, int64_t N, int64_t K, void *work_dev, size_t work_bytes,
+                               int32_t *min_out, cudaStream_t s);
+
+/*
  * rd_minplus_gemv -- y = x (x) B, the (min,+) product of a row vector x (K
  * entries, device, any alignment) with a K x N matrix B (ldb): y[j] =
  * min_k x[k] + B[k][j], y device (16-byte aligned), N entries; conventions and
@@ -249,6 +269,24 @@ rd_status rd_sparse_minplus(int R, int64_t M, const int64_t *block_start, const 
 rd_status rd_sparse_minplus_tma(int R, int64_t M, const int64_t *block_start, const uint32_t *records,
                                 const int16_t *B, int64_t ldb, int64_t N, int16_t *C, int64_t ldc, int32_t *min_out,
                                 int32_t *err_dev, cudaStream_t s);
+
+/*
+ * rd_sparse_minplus_tma_bounded -- rd_sparse_minplus_tma with its two
+ * failure-handling knobs exposed, so that the timeout path can be exercised
+ * without faulting or hanging a GPU: wait_limit (>= 1) is the number of
+ * mbarrier try_wait rounds after which a wait gives up (rd_sparse_minplus_tma
+ * uses 2^20), and stop_at (>= -1) makes each CTA's producer issue the copies of
+ * entries [0, stop_at) of its block and then stop, as a lost copy would (-1:
+ * never).  A consumer then waits for the missing entry, gives up after
+ * wait_limit rounds with no copy in flight, ORs 8 (the timeout bit) into
+ * *err_dev and ends its CTA; other CTAs see the bit and stop early.  Copies
+ * already issued are waited for before a CTA exits.  C is not valid after a
+ * timeout; the device and the context stay usable.
+ */
+rd_status rd_sparse_minplus_tma_bounded(int R, int64_t M, const int64_t *block_start, const uint32_t *records,
+                                        const int16_t *B, int64_t ldb, int64_t N, int16_t *C, int64_t ldc,
+                                        int32_t *min_out, int32_t *err_dev, uint32_t wait_limit, int32_t stop_at,
+                                        cudaStream_t s);
 
 /*
  * rd_power_until_periodic_sparse -- rd_power_until_periodic (same work buffer,
@@ -467,14 +505,21 @@ rd_status rd_server_destroy(rd_server *sv);
  * synchronise the whole device.  The paper has no counterpart; this is a
  * deployment convenience.
  *   Scratch: a static device array of RD_NOALLOC_SCRATCH_BYTES inside the
- *   library (its own module: reserved on a device once this entry point is first
- *   used there, and held until the process exits).  Problems that need more --
+ *   library, in a module of its own.  Under CUDA's lazy module loading (the
+ *   default, CUDA_MODULE_LOADING=LAZY) it is reserved on a device when this
+ *   entry point is first used there; with CUDA_MODULE_LOADING=EAGER every
+ *   process that loads the library reserves it on each device as the context is
+ *   created, whether or not it ever calls this entry point.  Either way it is
+ *   held until the process exits, and it lies outside the HBM budget that
+ *   rd_server admits jobs against.  Problems that need more --
  *   rd_power_work_bytes(N, lda, kmax, 2) > RD_NOALLOC_SCRATCH_BYTES -- are
  *   rejected with RD_ERR_NOMEM before any device work; within the limit the ring
  *   holds as many powers as fit (A(G) for m <= 7: 7 powers of N = 2507).
  *   Set-up: the first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call before
- *   any stream capture begins.
+ *   (cudaGetSymbolAddress) with that device current.
+ *   Synchronous: every call synchronises its stream and reads the search state
+ *   from the host between steps, so it must never be called while its stream
+ *   (or the legacy default stream) is being captured into a CUDA graph.
  *   Sharing: every call on a device uses the same array, which keeps the previous
  *   call's contents; each call re-initialises the state it reads, so no clearing
  *   is needed between calls.  Calls that overlap on the GPU (two host threads,
@@ -563,6 +608,42 @@ rd_status rd_tune_gemm(const int16_t *A, int64_t lda, const int16_t *B, int64_t 
  */
 rd_status rd_tune_split(rd_split_info_t *info, const void *plan_dev, const int16_t *B, int64_t ldb, int16_t *X_dev,
                         int64_t ldx, int16_t *C, int64_t ldc, int reps, rd_tune_entry_t *best, cudaStream_t s);
+
+/*
+ * rd_measure_addmin_peak -- the roofline denominator of the dense (min,+)
+ * product: the add-mins per SM clock and per second that the DPX unit retires
+ * on the current device.  The paper has no counterpart (its kernel ran on the
+ * scalar ALU of a Kepler GPU); the product's throughput is reported against
+ * this figure.  One full wave of CTAs (every SM at its resident limit) runs 16
+ * independent chains per thread of __viaddmin_s16x2 -- min(a + b, c) on both
+ * int16 halves of a word, 2 add-mins per instruction -- for 8 x trips steps per
+ * chain, register operands only, after a short warm-up launch.  *out gets:
+ *   addmin_per_clk_per_sm  add-mins per SM cycle, from each CTA's clock64()
+ *                          span (the slowest CTA counts), so it does not depend
+ *                          on the clock the GPU ran at;
+ *   addmin_per_s           add-mins per second of CUDA-event time;
+ *   sm_mhz                 the SM clock that implies (cycles / event time);
+ *   ms, sm_count, ctas_per_sm  as timed and launched;
+ *   lanes_per_clk_per_sm   the nominal DPX issue width, 64 s16x2 lanes per SM
+ *                          and clock, so the nominal peak is
+ *                          sm_count x 64 x 2 x clock.
+ * work_dev: device scratch (16-byte aligned, >= RD_PEAK_WORK_BYTES) for the
+ * per-CTA cycle counts.  trips in [1, 2^30]; 8192 takes about 17 ms on a
+ * GB300.  RD_ERR_ARG for bad arguments, RD_ERR_NOMEM for a short work buffer.
+ * Synchronous.
+ */
+#define RD_PEAK_WORK_BYTES 65536u
+typedef struct {
+  double addmin_per_clk_per_sm;
+  double addmin_per_s;
+  double sm_mhz;
+  double ms;
+  int32_t sm_count;
+  int32_t ctas_per_sm;
+  int32_t lanes_per_clk_per_sm;
+} rd_addmin_peak_t;
+rd_status rd_measure_addmin_peak(void *work_dev, size_t work_bytes, int64_t trips, rd_addmin_peak_t *out,
+                                 cudaStream_t s);
 
 /*
  * rd_gamma_R -- gamma_R(P_m box C_n) for m in [1, RD_MAX_M], n >= 3 (C_n needs

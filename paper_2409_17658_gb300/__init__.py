@@ -77,6 +77,9 @@ def _lib():
                                                        vp, vp, vp, vp]
         lib.rd_sparse_tune.argtypes = [vp, i64, i64, vp, sz, vp, vp, vp]
         lib.rd_sparse_minplus_tma.argtypes = [ctypes.c_int, i64, vp, vp, vp, i64, i64, vp, i64, vp, vp, vp]
+        lib.rd_sparse_minplus_tma_bounded.argtypes = [ctypes.c_int, i64, vp, vp, vp, i64, i64, vp, i64, vp, vp,
+                                                      ctypes.c_uint32, ctypes.c_int32, vp]
+        lib.rd_sparse_minplus_tma_bounded.restype = st
         lib.rd_split_default_j.argtypes = [ctypes.c_int]
         lib.rd_split_default_j.restype = ctypes.c_int
         lib.rd_split_plan_bytes.argtypes = [ctypes.c_int, ctypes.c_int, vp]
@@ -100,8 +103,14 @@ def _lib():
                      "rd_build_transfer_loss", "rd_minplus_gemm_batched", "rd_power_until_periodic_multi",
                      "rd_server_create", "rd_server_submit", "rd_server_wait", "rd_server_stats",
                      "rd_server_destroy", "rd_sparse_minplus_tma", "rd_minplus_gemv", "rd_split_plan_bytes",
-                     "rd_split_plan", "rd_split_minplus", "rd_power_until_periodic_split"):
+                     "rd_split_plan", "rd_split_minplus", "rd_power_until_periodic_split",
+                     "rd_measure_addmin_peak"):
             getattr(lib, name).restype = st
+        lib.rd_measure_addmin_peak.argtypes = [vp, sz, i64, vp, vp]
+        lib.rd_minplus_gemm_host_work_bytes.argtypes = [i64, i64, i64, vp]
+        lib.rd_minplus_gemm_host_work_bytes.restype = st
+        lib.rd_minplus_gemm_host.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, vp, sz, vp, vp]
+        lib.rd_minplus_gemm_host.restype = st
         _ = i32
         _LIB = lib
     return _LIB
@@ -302,6 +311,51 @@ class Server:
         self.close()
 
 
+def minplus_gemm_host_work_bytes(M: int, N: int, K: int) -> int:
+    out = ctypes.c_size_t()
+    _check(_lib().rd_minplus_gemm_host_work_bytes(M, N, K, ctypes.byref(out)), "rd_minplus_gemm_host_work_bytes")
+    return out.value
+
+
+def minplus_gemm_host(a, b, c, work, min_out=None, stream=None) -> None:
+    """rd_minplus_gemm_host: C = A (x) B with A, B, C in host memory (CPU tensors or numpy int16 arrays, pinned
+    for asynchronous copies), staged in the device tensor `work`.  Asynchronous on the stream."""
+    def host_ptr(x):
+        if hasattr(x, "data_ptr"):
+            if x.is_cuda:
+                raise ValueError("expected a host tensor")
+            return ctypes.c_void_p(x.data_ptr()), x.stride(0)
+        return ctypes.c_void_p(x.ctypes.data), x.strides[0] // 2
+
+    (pa, lda), (pb, ldb), (pc, ldc) = host_ptr(a), host_ptr(b), host_ptr(c)
+    M, K = a.shape
+    N = b.shape[1]
+    mo = _dptr(min_out) if min_out is not None else None
+    _check(_lib().rd_minplus_gemm_host(pa, lda, pb, ldb, pc, ldc, M, N, K, _dptr(work),
+                                       work.numel() * work.element_size(), mo, _stream(stream)),
+           "rd_minplus_gemm_host")
+
+
+class AddminPeak(ctypes.Structure):
+    _fields_ = [("addmin_per_clk_per_sm", ctypes.c_double), ("addmin_per_s", ctypes.c_double),
+                ("sm_mhz", ctypes.c_double), ("ms", ctypes.c_double), ("sm_count", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("lanes_per_clk_per_sm", ctypes.c_int32)]
+
+
+RD_PEAK_WORK_BYTES = 65536
+
+
+def measure_addmin_peak(trips: int = 8192, stream=None) -> dict:
+    """rd_measure_addmin_peak: the DPX add-min rate of the current device (per SM clock and per second)."""
+    import torch
+
+    work = torch.empty(RD_PEAK_WORK_BYTES, dtype=torch.uint8, device="cuda")
+    out = AddminPeak()
+    _check(_lib().rd_measure_addmin_peak(_dptr(work), RD_PEAK_WORK_BYTES, trips, ctypes.byref(out), _stream(stream)),
+           "rd_measure_addmin_peak")
+    return {f: getattr(out, f) for f, _ in AddminPeak._fields_}
+
+
 def power_work_bytes(n: int, ld: int, kmax: int, slots: int) -> int:
     out = ctypes.c_size_t()
     _check(_lib().rd_power_work_bytes(n, ld, kmax, slots, ctypes.byref(out)), "rd_power_work_bytes")
@@ -387,6 +441,17 @@ def sparse_minplus_tma(plan: dict, B, C, err, N: int | None = None, min_out=None
     _check(_lib().rd_sparse_minplus_tma(plan["R"], plan["M"], _dptr(plan["block_start"]), _dptr(plan["records"]),
                                         _dptr(B), B.stride(0), N, _dptr(C), C.stride(0), mo, _dptr(err),
                                         _stream(stream)), "rd_sparse_minplus_tma")
+
+
+def sparse_minplus_tma_bounded(plan: dict, B, C, err, wait_limit: int, stop_at: int, N: int | None = None,
+                               min_out=None, stream=None) -> None:
+    """sparse_minplus_tma with an explicit wait limit and producer stop point (the timeout path's test knobs)."""
+    N = C.shape[1] if N is None else N
+    mo = _dptr(min_out) if min_out is not None else None
+    _check(_lib().rd_sparse_minplus_tma_bounded(plan["R"], plan["M"], _dptr(plan["block_start"]),
+                                                _dptr(plan["records"]), _dptr(B), B.stride(0), N, _dptr(C),
+                                                C.stride(0), mo, _dptr(err), wait_limit, stop_at, _stream(stream)),
+           "rd_sparse_minplus_tma_bounded")
 
 
 def power_until_periodic_sparse(A, n: int, plan: dict, kmax: int, work, stream=None) -> dict:

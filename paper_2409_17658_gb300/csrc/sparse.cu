@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(128) sparse_minplus_kernel(SparseArgs a) {
 }
 
 template <int R, bool RING>
-__global__ void __launch_bounds__(kTmaThreads) sparse_tma_kernel(SparseArgs a, int32_t* err_plain) {
+__global__ void __launch_bounds__(kTmaThreads) sparse_tma_kernel(SparseArgs a, int32_t* err_plain, uint32_t wait_limit,
+                                                                  int stop_at) {
   const int16_t* B = a.B;
   int16_t* C = a.C;
   int32_t* err = err_plain;
@@ -164,21 +165,22 @@ __global__ void __launch_bounds__(kTmaThreads) sparse_tma_kernel(SparseArgs a, i
     err = &a.st->err;
   }
   if (*(volatile const int32_t*)err & kErrTimeout) return;  // an earlier CTA gave up: the launch is void
-  sparse_tma_tile_body<R>(a, B, C, blockIdx.x, blockIdx.y, err);
+  sparse_tma_tile_body<R>(a, B, C, blockIdx.x, blockIdx.y, err, wait_limit, stop_at);
 }
 
 template <bool RING>
-cudaError_t launch_sparse_tma(int R, const SparseArgs& a, int32_t* err, cudaStream_t s) {
+cudaError_t launch_sparse_tma(int R, const SparseArgs& a, int32_t* err, cudaStream_t s, uint32_t wait_limit = kWaitLimit,
+                              int stop_at = -1) {
   const int64_t nb = (a.M + R - 1) / R;
   const int64_t gy = (a.Ncols + kSlabCols - 1) / kSlabCols;
   if (nb <= 0 || gy <= 0) return cudaSuccess;
   if (nb > 0x7FFFFFFF || gy > 65535) return cudaErrorInvalidConfiguration;
   const dim3 grid((unsigned)nb, (unsigned)gy);
   switch (R) {
-    case 1: sparse_tma_kernel<1, RING><<<grid, kTmaThreads, kTmaSmemBytes, s>>>(a, err); break;
-    case 2: sparse_tma_kernel<2, RING><<<grid, kTmaThreads, kTmaSmemBytes, s>>>(a, err); break;
-    case 4: sparse_tma_kernel<4, RING><<<grid, kTmaThreads, kTmaSmemBytes, s>>>(a, err); break;
-    case 8: sparse_tma_kernel<8, RING><<<grid, kTmaThreads, kTmaSmemBytes, s>>>(a, err); break;
+    case 1: sparse_tma_kernel<1, RING><<<grid, kTmaThreads, kTmaSmemBytes, s>>>(a, err, wait_limit, stop_at); break;
+    case 2: sparse_tma_kernel<2, RING><<<grid, kTmaThreads, kTmaSmemBytes, s>>>(a, err, wait_limit, stop_at); break;
+    case 4: sparse_tma_kernel<4, RING><<<grid, kTmaThreads, kTmaSmemBytes, s>>>(a, err, wait_limit, stop_at); break;
+    case 8: sparse_tma_kernel<8, RING><<<grid, kTmaThreads, kTmaSmemBytes, s>>>(a, err, wait_limit, stop_at); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -315,10 +317,12 @@ extern "C" rd_status rd_sparse_minplus(int R, int64_t M, const int64_t* block_st
   return RD_OK;
 }
 
-extern "C" rd_status rd_sparse_minplus_tma(int R, int64_t M, const int64_t* block_start, const uint32_t* records,
-                                           const int16_t* B, int64_t ldb, int64_t N, int16_t* C, int64_t ldc,
-                                           int32_t* min_out, int32_t* err_dev, cudaStream_t s) {
+extern "C" rd_status rd_sparse_minplus_tma_bounded(int R, int64_t M, const int64_t* block_start,
+                                                   const uint32_t* records, const int16_t* B, int64_t ldb, int64_t N,
+                                                   int16_t* C, int64_t ldc, int32_t* min_out, int32_t* err_dev,
+                                                   uint32_t wait_limit, int32_t stop_at, cudaStream_t s) {
   if (!valid_r(R) || M < 0 || N < 0 || !err_dev) return RD_ERR_ARG;
+  if (wait_limit < 1 || stop_at < -1) return RD_ERR_ARG;
   if (M > 0 && N > 0) {
     if (!block_start || !records || !B || !C) return RD_ERR_ARG;
     if (!aligned16(B) || !aligned16(C) || !aligned16(records) || ldb < N || ldb % 8 != 0 || ldc < N ||
@@ -341,9 +345,16 @@ extern "C" rd_status rd_sparse_minplus_tma(int R, int64_t M, const int64_t* bloc
   a.ldc = ldc;
   a.Ncols = N;
   a.min_out = min_out;
-  e = launch_sparse_tma<false>(R, a, err_dev, s);
+  e = launch_sparse_tma<false>(R, a, err_dev, s, wait_limit, stop_at);
   if (e != cudaSuccess) return cuda_fail(e);
   return RD_OK;
+}
+
+extern "C" rd_status rd_sparse_minplus_tma(int R, int64_t M, const int64_t* block_start, const uint32_t* records,
+                                           const int16_t* B, int64_t ldb, int64_t N, int16_t* C, int64_t ldc,
+                                           int32_t* min_out, int32_t* err_dev, cudaStream_t s) {
+  return rd_sparse_minplus_tma_bounded(R, M, block_start, records, B, ldb, N, C, ldc, min_out, err_dev, kWaitLimit, -1,
+                                       s);
 }
 
 extern "C" rd_status rd_power_until_periodic_sparse(const int16_t* A_dev, int64_t N, int64_t lda, int R,

@@ -172,7 +172,10 @@ __device__ __forceinline__ void sparse_tile_body(const SparseArgs& a, const int1
 // longer go through the SM's load/store path, and up to kStages row segments per CTA
 // are in flight without holding registers.  Every wait is bounded: past the bound the
 // kernel sets kErrTimeout in *err, stops, waits (bounded again) for the copies it has
-// in flight, and returns, so a fault in the protocol cannot hang the GPU.
+// in flight, and returns, so a fault in the protocol cannot hang the GPU.  The bound
+// (wait_limit) and a stop point for the producer (stop_at: it issues entries
+// [0, stop_at) of each block and no more; -1 for none) are kernel arguments, so a
+// test can make the consumers' wait run out with no copy in flight.
 
 constexpr int kStages = 16;
 constexpr int kTmaConsumers = 64;                  // two warps, 16 columns per thread
@@ -181,7 +184,7 @@ constexpr int kSlabCols = kTmaConsumers * 16;      // 1024 columns per CTA
 constexpr int kRecordSlot = 64;                    // bytes reserved for the record in a stage
 constexpr int kStageBytes = kRecordSlot + kSlabCols * 2;
 constexpr size_t kTmaSmemBytes = (size_t)kStages * kStageBytes + 2 * kStages * sizeof(uint64_t);
-constexpr uint32_t kWaitLimit = 1u << 20;          // try_wait rounds before a wait gives up
+constexpr uint32_t kWaitLimit = 1u << 20;          // try_wait rounds before a wait gives up (default)
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -194,11 +197,11 @@ __device__ __forceinline__ void mbar_arrive_expect(uint32_t bar, uint32_t bytes)
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
-// true once the phase of parity `parity` has completed; false after kWaitLimit tries, or as
+// true once the phase of parity `parity` has completed; false after `limit` tries, or as
 // soon as another CTA has reported a timeout in *err (checked every 1024 tries; err may be null),
 // so that one failure ends the whole launch quickly
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const int32_t* err) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const int32_t* err, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     if (err != nullptr && (it & 1023u) == 1023u && (*(volatile const int32_t*)err & kErrTimeout)) return false;
     uint32_t done;
     asm volatile(
@@ -219,7 +222,7 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uin
 template <int R>
 __device__ __forceinline__ void sparse_tma_tile_body(const SparseArgs& a, const int16_t* __restrict__ B,
                                                      int16_t* __restrict__ C, const int64_t b, const int64_t slab,
-                                                     int32_t* err) {
+                                                     int32_t* err, uint32_t wait_limit, int stop_at) {
   constexpr int W = record_words(R);
   constexpr uint32_t kRecBytes = W * 4;
   extern __shared__ __align__(128) unsigned char tsm[];
@@ -258,17 +261,19 @@ __device__ __forceinline__ void sparse_tma_tile_body(const SparseArgs& a, const 
   if (tid >= kTmaConsumers) {
     // producer warp: lanes fetch the next 32 entries' columns, lane 0 issues the copies
     const int lane = tid - kTmaConsumers;
+    const int n_issue = (stop_at >= 0 && stop_at < n_e) ? stop_at : n_e;
     int issued = 0, fail = 0;
-    for (int base = 0; base < n_e && !fail; base += 32) {
+    for (int base = 0; base < n_issue && !fail; base += 32) {
       const int e = base + lane;
       const uint32_t t_lane = (e < n_e) ? __ldg(a.rec + (e0 + e) * W) : 0u;
-      const int cnt = (n_e - base < 32) ? (n_e - base) : 32;
+      const int cnt = (n_issue - base < 32) ? (n_issue - base) : 32;
       for (int u = 0; u < cnt; ++u) {
         const uint32_t t = __shfl_sync(0xFFFFFFFFu, t_lane, u);
         int f = 0;
         if (lane == 0) {
           const int i = base + u, slot = i % kStages;
-          if (i >= kStages && !mbar_wait(saddr(&empty[slot]), (uint32_t)((i / kStages) & 1) ^ 1u, err)) {
+          if (i >= kStages &&
+              !mbar_wait(saddr(&empty[slot]), (uint32_t)((i / kStages) & 1) ^ 1u, err, wait_limit)) {
             f = 1;
           } else {
             unsigned char* stg = tsm + (size_t)slot * kStageBytes;
@@ -296,7 +301,8 @@ __device__ __forceinline__ void sparse_tma_tile_body(const SparseArgs& a, const 
     int i = 0;
     for (; i < n_e; ++i) {
       const int slot = i % kStages;
-      if (*(volatile int*)&failed_sh || !mbar_wait(saddr(&full[slot]), (uint32_t)((i / kStages) & 1), err)) {
+      if (*(volatile int*)&failed_sh ||
+          !mbar_wait(saddr(&full[slot]), (uint32_t)((i / kStages) & 1), err, wait_limit)) {
         atomicOr(err, kErrTimeout);
         atomicOr(&failed_sh, 1);
         break;
@@ -322,8 +328,8 @@ __device__ __forceinline__ void sparse_tma_tile_body(const SparseArgs& a, const 
   // after a failure: let every issued copy land before the CTA's shared memory is released
   if (tid == 0 && failed_sh) {
     const int done = consumed_sh[0] < consumed_sh[1] ? consumed_sh[0] : consumed_sh[1];
-    for (int i = done; i < issued_sh; ++i)  // bounded, but not cut short by the error flag
-      mbar_wait(saddr(&full[i % kStages]), (uint32_t)((i / kStages) & 1), nullptr);
+    for (int i = done; i < issued_sh; ++i)  // bounded by the default limit, not cut short by the error flag
+      mbar_wait(saddr(&full[i % kStages]), (uint32_t)((i / kStages) & 1), nullptr, kWaitLimit);
   }
 
   int32_t lmin = kInf, ldiag = kInf;
