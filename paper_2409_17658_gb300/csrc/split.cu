@@ -461,6 +461,21 @@ __device__ inline uint64_t group_key(const int32_t* r) {
   return key;
 }
 
+// Correct words of length len at compile time, by their last letter: a may follow a or c, b may follow c
+// or d, c anything, d anything but a (Definition 4 forbids ad, da, ab, ba, bb).
+constexpr int64_t correct_count_ce(int len) {
+  int64_t a = 1, b = 1, c = 1, d = 1;
+  for (int i = 1; i < len; ++i) {
+    const int64_t a2 = a + c, b2 = c + d, c2 = a + b + c + d, d2 = b + c + d;
+    a = a2; b = b2; c = c2; d = d2;
+  }
+  return len == 0 ? 1 : a + b + c + d;
+}
+static_assert(correct_count_ce(3) == 33 && correct_count_ce(9) == 21909, "word count recurrence");
+// group_order_kernel keeps one 8-byte key per group of a fiber (at most C_(kSplitMaxLen - 1) groups) in
+// dynamic shared memory without raising the 48 KB default limit.
+static_assert(8 * correct_count_ce(kSplitMaxLen - 1) <= 48 * 1024, "group keys exceed 48 KB of shared memory");
+
 // One CTA per fiber: the groups' keys in shared memory, then each group's rank (the groups with a smaller
 // key, or an equal key and a smaller index) is its place in the order.
 __global__ void group_order_kernel(const int32_t* gls, int64_t n_groups, uint16_t* ord) {

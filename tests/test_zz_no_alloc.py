@@ -3,9 +3,11 @@
 For callers that cannot allocate device memory (their memory belongs to another
 allocator, or allocation is forbidden or too slow where they run).  The entry
 point is called through the C ABI and its results are compared with those of
-rd_power_until_periodic, which uses a caller-owned work buffer, on two calls in
-a row (a larger problem first, so the second call starts from the first one's
-leftover scratch contents).  This file is collected last on purpose.
+rd_power_until_periodic, which uses a caller-owned work buffer, and with the CPU
+oracle, on three calls in a row: m = 7 and m = 5 take the multi-kernel dense
+step (the larger first, so the second starts from the first one's leftover
+scratch contents), and m = 3 the single-CTA search.  This file is collected last
+on purpose.
 """
 import ctypes
 
@@ -49,16 +51,19 @@ def call_with_work(lib, torch, rd, A, n, kmax):
     return st, gamma, (k.value, p.value, q.value)
 
 
-def test_noalloc_matches_work_buffer_entry_point(lib_and_torch):
+def test_noalloc_matches_work_buffer_entry_point(lib_and_torch, orc):
     rd, lib, torch = lib_and_torch
     kmax = 48
-    for m in (6, 3):  # two calls in a row, the larger problem first
+    for m in (7, 5, 3):  # calls in a row, the larger problems first
         A, n = rd.transfer_matrix(m)
         st_ref, g_ref, t_ref = call_with_work(lib, torch, rd, A, n, kmax)
         st, g, t = call_noalloc(lib, torch, A, n, kmax)
         assert st_ref == rd.RD_OK
         assert st == st_ref and t == t_ref, (m, st, t, t_ref)
         assert np.array_equal(g, g_ref), m  # integer results: exact
+        o = orc.power_until_periodic(m, kmax=kmax)
+        assert t == (o["k"], o["p"], o["q"]), (m, t, o)
+        assert np.array_equal(g[1:o["j"] + 1], o["gamma"][1:o["j"] + 1]), m
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch(lib_and_torch):
