@@ -43,7 +43,19 @@ PEAK_GOPS = SMS * DPX_LANES_PER_CLK * ADDMIN_PER_LANE * SM_MAX_MHZ * 1e6 / 1e9
 # dram__bytes_read.sum and dram__bytes_write.sum on that launch (8.60 GB read + 0.552 GB written).
 GEMM_TRAFFIC_BYTES = 9.152e9
 CONFIG_NAME = "synthetic dense (min,+) GEMM N=16384, int16 uniform[0,32], P(inf)=0.5"
-HBM_GBS = 6652.3  # measured copy bandwidth of the GB300s (STREAM-style, read + write)
+
+
+def _measured_hbm_gbs() -> float:
+    """The measured copy bandwidth of the GB300s (MEASURED_PEAKS.json beside this script, read + write
+    bytes), else the earlier measurement of 6652.3 GB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6652.3
+
+
+HBM_GBS = _measured_hbm_gbs()
 
 
 def max_over_ranks(value_ms: float, dist, device) -> float:
@@ -191,6 +203,14 @@ def time_to_period(rd, torch, ms: list[int], with_oracle: bool) -> dict:
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
         products = r["j"] - 1
+        # the A(G) builder alone (a store stream: 2 N ld bytes written)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record()
+        for _ in range(3):
+            rd.build_transfer(m, A)
+        b1.record()
+        torch.cuda.synchronize()
+        build_ms = b0.elapsed_time(b1) / 3
         if small:
             plan = rd.split_plan(m, x_ld=ld)  # for the product timed alone below
         info = plan["info"]
@@ -209,6 +229,8 @@ def time_to_period(rd, torch, ms: list[int], with_oracle: bool) -> dict:
                  "step": ("single-CTA search (N <= 128)" if small else
                           f"row split j={info.j} (w {info.w1}/{info.w2}, slabs per CTA {info.k1}/{info.k2})"),
                  "us_per_power": dt / r["j"] * 1e6, "tuned_shape": tuned,
+                 "build_ms": build_ms, "build_GBps": 2.0 * n * ld / (build_ms * 1e-3) / 1e9,
+                 "build_frac_of_measured_hbm": 2.0 * n * ld / (build_ms * 1e-3) / 1e9 / HBM_GBS,
                  "split_product_ms": prod_ms, "split_x_rows": info.x_rows,
                  "split_product_GBps": moved / (prod_ms * 1e-3) / 1e9,
                  "split_product_frac_of_measured_hbm": moved / (prod_ms * 1e-3) / 1e9 / HBM_GBS,
@@ -501,53 +523,113 @@ def batched_products(rd, torch, count: int = 64, seed: int = 4) -> dict:
     return out
 
 
-def serving(rd, queries: int = 20000, rate: float = 20000.0, seed: int = 7, budget_gb: float = 120.0) -> dict:
-    """A Poisson stream of gamma_R(P_m box C_n) queries through the query server.
-
-    m uniform in {2..9} and n uniform in [3, 200]; one query in 20 is m = 10 with n = 0 mod 5 (its
-    footprint, 76 GB, fits the budget).  Phase "cold" starts from a fresh server (first queries of each m
-    trigger its period search; searches share the GPU step by step); phase "warm" replays the stream
-    against the settled server.  Latency is measured by the server from submit to answer.
-    """
+def query_mix(queries: int, seed: int):
+    """Config 5's query mix: m uniform in {2..9}, n uniform in [3, 200]; one query in 20 is m = 10 with
+    n = 0 mod 5 in [10, 200] (N(10)^2 int16 = 8.4 GB fits HBM).  Also unit exponential gaps for the arrivals."""
     from paper_2409_17658_gb300 import inputs
 
     x = inputs.splitmix64((np.uint64(seed) << np.uint64(32)) + np.arange(4 * queries, dtype=np.uint64))
     u = (x >> np.uint64(11)).astype(np.float64) / float(1 << 53)
-    gaps = -np.log1p(-u[:queries]) / rate
-    arrivals = np.cumsum(gaps)
+    gaps = -np.log1p(-u[:queries])
     ms = (2 + (u[queries:2 * queries] * 8).astype(np.int64)).astype(np.int32)
     ns = (3 + (u[2 * queries:3 * queries] * 198).astype(np.int64)).astype(np.int64)
     ten = u[3 * queries:] < 0.05
     ms[ten] = 10
     ns[ten] = 10 + 5 * (ns[ten] % 39)
-    out = {"queries": queries, "rate_per_s": rate, "budget_gb": budget_gb}
+    return ms, ns, gaps
+
+
+def serve_stream(rd, ms, ns, arrivals, budget_gb: float, server=None) -> dict:
+    """Submits the queries at their arrival times to a server (a fresh one unless given) and waits for all."""
+    sv = server or rd.Server(hbm_budget_bytes=int(budget_gb * (1 << 30)), kmax=128)
+    try:
+        tickets = []
+        t0 = time.perf_counter()
+        i, q = 0, len(ms)
+        while i < q:
+            now = time.perf_counter() - t0
+            j = int(np.searchsorted(arrivals, now, side="right"))
+            if j <= i:
+                time.sleep(max(0.0, min(arrivals[i] - now, 0.001)))
+                continue
+            tickets.append(sv.submit(ms[i:j], ns[i:j]))
+            i = j
+        g, st, lat = sv.wait(np.concatenate(tickets), timeout_s=900)
+        wall = time.perf_counter() - t0
+        stats = sv.stats()
+    finally:
+        if server is None:
+            sv.close()
+    return {"gamma": g, "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "max_ms": float(lat.max() * 1e3), "queries_per_s": q / wall, "wall_s": wall,
+            "all_ok": bool(np.all(st == rd.RD_OK)), "jobs": int(stats["jobs_admitted"]),
+            "peak_gb": stats["bytes_peak"] / 2 ** 30}
+
+
+def plain_stream(rd, ms, ns, arrivals) -> dict:
+    """The plain path on the same stream: one rd_gamma_R call per query, in arrival order, one at a time, from
+    a cleared cache (each m's first query runs its whole period search before the next query starts)."""
+    rd.gamma_R_clear()
+    q = len(ms)
+    g = np.zeros(q, dtype=np.int64)
+    lat = np.zeros(q)
+    t0 = time.perf_counter()
+    for i in range(q):
+        now = time.perf_counter() - t0
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        g[i] = rd.gamma_R(int(ms[i]), int(ns[i]))
+        lat[i] = time.perf_counter() - t0 - arrivals[i]
+    wall = time.perf_counter() - t0
+    return {"gamma": g, "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "max_ms": float(lat.max() * 1e3), "queries_per_s": q / wall, "wall_s": wall}
+
+
+def serving(rd, queries: int = 3000, rates=(1e3, 1e4, 1e5, 1e6), seed: int = 7, budget_gb: float = 120.0) -> dict:
+    """Config 5: Poisson streams of gamma_R(P_m box C_n) queries through the query server, swept over the
+    offered rate.  Every rate starts a fresh server, so each m's first queries trigger its period search
+    (searches of different m share the GPU step by step, admitted by HBM footprint) and the rest wait for
+    it or are answered from its result.  Beside the sweep, at the highest rate: the plain path (one
+    rd_gamma_R per query, one at a time, cleared cache) on the same stream, whose answers every served
+    answer must equal; and a warm replay against a settled server.  Latency is submit to answer.
+    """
+    ms, ns, gaps = query_mix(queries, seed)
+    out = {"queries": queries, "budget_gb": budget_gb, "mix": "m uniform 2..9, n uniform 3..200; 5 % m = 10, n = 0 mod 5"}
+    sweep, answers = [], []
+    for rate in rates:
+        arrivals = np.cumsum(gaps / rate)
+        r = serve_stream(rd, ms, ns, arrivals, budget_gb)
+        answers.append(r.pop("gamma"))
+        sweep.append({"offered_per_s": rate, **r})
+    out["sweep"] = sweep
+    arrivals = np.cumsum(gaps / rates[-1])
+    plain = plain_stream(rd, ms, ns, arrivals)
+    want = plain.pop("gamma")
+    out["plain_at_max_rate"] = plain
+    out["served_over_plain_at_max_rate"] = sweep[-1]["queries_per_s"] / plain["queries_per_s"]
+    # the plain path without a cache (Algorithm 2 and the closed form for every query, one at a time), on a
+    # bounded sample: the first queries of the stream, all arrived at once
+    sample = 60
+    uncached_ok = True
+    t0 = time.perf_counter()
+    for i in range(sample):
+        rd.gamma_R_clear()
+        uncached_ok &= rd.gamma_R(int(ms[i]), int(ns[i])) == want[i]
+    dt = time.perf_counter() - t0
+    out["plain_uncached_sample"] = {"queries": sample, "queries_per_s": sample / dt, "wall_s": dt,
+                                    "m10_queries": int(np.sum(ms[:sample] == 10))}
+    out["served_over_plain_uncached"] = sweep[-1]["queries_per_s"] / (sample / dt)
+    out["answers_equal_plain"] = bool(uncached_ok and all(np.array_equal(a, want) for a in answers))
+    tens = np.nonzero(ms == 10)[0]
+    out["m10_cor12_holds"] = bool(all(5 * want[i] == 22 * ns[i] for i in tens))
     sv = rd.Server(hbm_budget_bytes=int(budget_gb * (1 << 30)), kmax=128)
     try:
-        for phase in ("cold", "warm"):
-            tickets = []
-            t0 = time.perf_counter()
-            i = 0
-            while i < queries:
-                now = time.perf_counter() - t0
-                j = int(np.searchsorted(arrivals, now, side="right"))
-                if j <= i:
-                    time.sleep(max(0.0, min(arrivals[i] - now, 0.001)))
-                    continue
-                tickets.append(sv.submit(ms[i:j], ns[i:j]))
-                i = j
-            g, st, lat = sv.wait(np.concatenate(tickets), timeout_s=900)
-            wall = time.perf_counter() - t0
-            out[phase] = {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                          "max_ms": float(lat.max() * 1e3), "queries_per_s": queries / wall, "wall_s": wall,
-                          "all_ok": bool(np.all(st == rd.RD_OK))}
-        out["stats"] = sv.stats()
+        serve_stream(rd, ms, ns, np.zeros(queries), budget_gb, server=sv)  # settle every m
+        warm = serve_stream(rd, ms, ns, arrivals, budget_gb, server=sv)
+        warm.pop("gamma")
+        out["warm_at_max_rate"] = warm
     finally:
         sv.close()
-    rng = np.random.default_rng(seed)
-    pick = rng.choice(np.nonzero(ms <= 9)[0], 200, replace=False)
-    out["answers_match_alone"] = bool(all(g[i] == rd.gamma_R(int(ms[i]), int(ns[i])) for i in pick))
-    tens = np.nonzero(ms == 10)[0]
-    out["m10_cor12_holds"] = bool(all(5 * g[i] == 22 * ns[i] for i in tens))
     return out
 
 
@@ -602,6 +684,8 @@ def main() -> None:
                     help="time only the row-split product at m = M (profiling aid)")
     ap.add_argument("--tune", action="store_true", help="with --split-only: run the autotuner on the plan first")
     ap.add_argument("--batched-only", action="store_true", help="time only the 64-product batch (profiling aid)")
+    ap.add_argument("--build-only", type=int, default=0, metavar="M",
+                    help="time only the A(G) builder at m = M (profiling aid)")
     ap.add_argument("--tune-table", default="", metavar="PATH",
                     help="load a saved tuning table (JSON, paper_2409_17658_gb300.tuning) before running")
     ap.add_argument("--no-sweep", action="store_true", help="skip the dense sweep at the other sizes")
@@ -627,6 +711,23 @@ def main() -> None:
         return run_split_only(rd, torch, args)
     if args.batched_only:
         return run_batched_only(rd, torch, args)
+    if args.build_only:
+        m = args.build_only
+        n = rd.state_count(m)
+        ld = rd.padded_dim(n)
+        A = torch.empty((n, ld), dtype=torch.int16, device="cuda")
+        for _ in range(max(args.warmup, 1)):
+            rd.build_transfer(m, A)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            rd.build_transfer(m, A)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_ = e0.elapsed_time(e1) / args.steps
+        print(json.dumps({"build_only": m, "N": n, "ms": ms_, "GBps": 2.0 * n * ld / (ms_ * 1e-3) / 1e9,
+                          "frac_of_measured_hbm": 2.0 * n * ld / (ms_ * 1e-3) / 1e9 / HBM_GBS}))
+        return
     if args.gemv_only:
         from paper_2409_17658_gb300 import inputs
 

@@ -659,6 +659,10 @@ rd_status rd_measure_addmin_peak(void *work_dev, size_t work_bytes, int64_t trip
  */
 rd_status rd_gamma_R(int m, int64_t n, int64_t *out);
 
+/* rd_gamma_R_clear -- forgets every cached m, so the next rd_gamma_R(m, .) runs its period search again
+ * (a cold start, e.g. for timing).  Thread-safe; waits for a search in progress. */
+rd_status rd_gamma_R_clear(void);
+
 #ifdef __cplusplus
 }
 #endif

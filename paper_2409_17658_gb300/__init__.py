@@ -107,6 +107,8 @@ def _lib():
                      "rd_measure_addmin_peak"):
             getattr(lib, name).restype = st
         lib.rd_measure_addmin_peak.argtypes = [vp, sz, i64, vp, vp]
+        lib.rd_gamma_R_clear.argtypes = []
+        lib.rd_gamma_R_clear.restype = st
         lib.rd_minplus_gemm_host_work_bytes.argtypes = [i64, i64, i64, vp]
         lib.rd_minplus_gemm_host_work_bytes.restype = st
         lib.rd_minplus_gemm_host.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, vp, sz, vp, vp]
@@ -618,6 +620,11 @@ def gamma_R(m: int, n: int) -> int:
     out = ctypes.c_int64()
     _check(_lib().rd_gamma_R(m, n, ctypes.byref(out)), "rd_gamma_R")
     return out.value
+
+
+def gamma_R_clear() -> None:
+    """rd_gamma_R_clear: forget every cached m (the next rd_gamma_R of each m searches again)."""
+    _check(_lib().rd_gamma_R_clear(), "rd_gamma_R_clear")
 
 
 # ---------------------------------------------------------------- allocation helpers (torch owns device memory)

@@ -485,6 +485,12 @@ rd_status compute_cached(int m, Cached* out) {
 }
 }  // namespace
 
+extern "C" rd_status rd_gamma_R_clear(void) {
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  for (auto& c : g_cache) c = Cached{};
+  return RD_OK;
+}
+
 extern "C" rd_status rd_gamma_R(int m, int64_t n, int64_t* out) {
   if (m < 1 || m > RD_MAX_M || n < 3 || !out) return RD_ERR_ARG;
   std::lock_guard<std::mutex> lock(g_cache_mu);

@@ -120,71 +120,119 @@ __device__ inline int newly_dominated(const Masks& q, const Masks& p) {
          3 * __popc(q.d & p.a) + (int)(p.a & 1u);
 }
 
-// Tile of 64 rows (q) x 256 columns (p).  Thread (tx, ty): columns 8 tx .. 8 tx + 7,
-// rows ty, ty + 8, ..., one 16-byte store per row.  LOSS selects the Appendix variant,
-// whose labels 10 p(a) + 5 p(b) - 2 nd(q,p) are stored shifted by 2m (never negative).
-constexpr int kTq = 64, kTp = 256;
+// The destination side of "p can follow q", per word p: the rows where a letter of q is NOT satisfied by
+// p (Sec. 4.A, as in can_follow): q has an arc to p iff q.a & na | q.b & nb | q.c & nc | q.d & nd == 0.
+struct Refuse {
+  uint32_t na, nb, nc, nd;
+};
+
+__device__ inline Refuse refuse_masks(const Masks& p, uint32_t full) {
+  const uint32_t near_a = ((p.a << 1) | (p.a >> 1)) & full;
+  const uint32_t c_with_a = p.c & near_a;
+  return Refuse{~(p.a | p.c), ~(p.d | c_with_a), ~(p.a | p.b | p.d | c_with_a), ~p.a};
+}
+
+// r-th correct word, unranked against the word table held in shared memory (t[len * 4 + c]; every count
+// is below 2^31 for m <= RD_MAX_M).
+__device__ inline uint32_t unrank_sm(const int32_t* t, int m, int32_t r) {
+  uint32_t code = 0;
+  int prev = -1;
+  for (int i = 1; i <= m; ++i) {
+    const int len = m - i + 1;
+    for (int c = 0; c < 4; ++c) {
+      if (prev >= 0 && !pair_allowed(prev, c)) continue;
+      const int32_t cnt = t[len * 4 + c];
+      if (r < cnt) {
+        code = (code << 2) | (uint32_t)c;
+        prev = c;
+        break;
+      }
+      r -= cnt;
+    }
+  }
+  return code;
+}
+
+// A CTA writes a band of `rows` (<= kBuildMaxRows) rows (q) x kBuildCols columns (p), one 16-byte store per
+// row and thread: thread t owns columns 8t .. 8t + 7 of the band, keeps those 8 destination words' refusal
+// masks and labels in registers, and sweeps the band's rows, whose letter masks it reads from shared memory
+// (the same word for every thread: a broadcast).  Per entry: four masked tests, a compare and a select.
+// The band's words are unranked once (8 per thread for the columns, one per thread for the rows), so the
+// prologue is small against the band's 16-byte stores.  LOSS selects the Appendix variant, whose labels
+// 10 p(a) + 5 p(b) - 2 nd(q,p) are stored shifted by 2m (never negative).
+constexpr int kBuildThreads = 256;
+constexpr int kBuildCols = kBuildThreads * 8;
+constexpr int kBuildMaxRows = kBuildThreads;
 
 template <bool LOSS>
-__global__ void __launch_bounds__(256) transfer_kernel(WordTable w, int64_t n, int16_t* A, int64_t lda,
-                                                       int64_t ptiles) {
-  __shared__ Masks qm[kTq];
-  __shared__ Masks pm[kTp];
-  __shared__ int16_t pw[kTp];
-  const int64_t tile = blockIdx.x;
-  const int64_t q0 = (tile / ptiles) * kTq, p0 = (tile % ptiles) * kTp;
+__global__ void __launch_bounds__(kBuildThreads) transfer_kernel(WordTable w, int64_t n, int16_t* A, int64_t lda,
+                                                                 int64_t ctiles, int rows_per_cta) {
+  __shared__ int32_t tab[(RD_MAX_M + 1) * 4];
+  __shared__ uint4 qm[kBuildMaxRows];
   const int tid = threadIdx.x;
-  for (int i = tid; i < kTq + kTp; i += blockDim.x) {
-    if (i < kTq) {
-      const int64_t q = q0 + i;
-      qm[i] = (q < n) ? word_masks(unrank(w, q), w.m) : Masks{0, 0, 0, 0};
+  for (int i = tid; i < (w.m + 1) * 4; i += kBuildThreads) tab[i] = (int32_t)w.t[i >> 2][i & 3];
+  __syncthreads();
+  const int64_t q0 = (int64_t)(blockIdx.x / ctiles) * rows_per_cta;
+  const int64_t pc = (int64_t)(blockIdx.x % ctiles) * kBuildCols + 8 * tid;
+  if (tid < rows_per_cta) {
+    const int64_t q = q0 + tid;
+    Masks k{0, 0, 0, 0};
+    if (q < n) k = word_masks(unrank_sm(tab, w.m, (int32_t)q), w.m);
+    qm[tid] = make_uint4(k.a, k.b, k.c, k.d);
+  }
+  const uint32_t full = (w.m >= 32) ? 0xFFFFFFFFu : ((1u << w.m) - 1u);
+  Refuse rf[8];
+  Masks pk[8];
+  int16_t wt[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int64_t p = pc + e;
+    if (p < n) {
+      pk[e] = word_masks(unrank_sm(tab, w.m, (int32_t)p), w.m);
+      rf[e] = refuse_masks(pk[e], full);
+      wt[e] = (int16_t)word_weight(pk[e]);
     } else {
-      const int j = i - kTq;
-      const int64_t p = p0 + j;
-      if (p < n) {
-        pm[j] = word_masks(unrank(w, p), w.m);
-        pw[j] = (int16_t)word_weight(pm[j]);
-      } else {
-        pm[j] = Masks{0, 0, 0, 0};
-        pw[j] = kInf;
-      }
+      pk[e] = Masks{0, 0, 0, 0};
+      rf[e] = Refuse{~0u, ~0u, ~0u, ~0u};  // every row refuses: no arc into a padding column
+      wt[e] = kInf;
     }
   }
   __syncthreads();
-  const uint32_t full = (w.m >= 32) ? 0xFFFFFFFFu : ((1u << w.m) - 1u);
-  const int tx = tid & 31, ty = tid >> 5;
-  const int64_t pc = p0 + 8 * tx;
   if (pc >= lda) return;
-  // this thread's 8 destination words, read from shared memory once for all its rows (the lanes' words
-  // are 8 apart, so every such read is a bank-conflicted one)
-  Masks pj[8];
-  int16_t wj[8];
-#pragma unroll
-  for (int e = 0; e < 8; ++e) {
-    pj[e] = pm[8 * tx + e];
-    wj[e] = pw[8 * tx + e];
-  }
-  for (int r = ty; r < kTq; r += 8) {
-    const int64_t q = q0 + r;
-    if (q >= n) break;
-    const Masks qf = LOSS ? relax_last_row(qm[r]) : qm[r];
+  const int rows = (int)((n - q0 < rows_per_cta) ? (n - q0) : rows_per_cta);
+  int16_t* dst = A + q0 * lda + pc;
+  for (int r = 0; r < rows; ++r, dst += lda) {
+    const uint4 qv = qm[r];
+    Masks qf{qv.x, qv.y, qv.z, qv.w};
+    if (LOSS) qf = relax_last_row(qf);  // the follow rule of the variant; Algorithm 3 takes q as it is
     uint32_t packed[4];
 #pragma unroll
     for (int e = 0; e < 8; e += 2) {
-      int16_t v[2];
+      uint32_t v[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int j = 8 * tx + e + h;
-        const bool arc = (p0 + j < n) && can_follow(qf, pj[e + h], full);
-        int label = wj[e + h];
+        const Refuse& f = rf[e + h];
+        const uint32_t bad = (qf.a & f.na) | (qf.b & f.nb) | (qf.c & f.nc) | (qf.d & f.nd);
+        int label = wt[e + h];
         if (LOSS)
-          label = 10 * __popc(pj[e + h].a) + 5 * __popc(pj[e + h].b) - 2 * newly_dominated(qm[r], pj[e + h]) + 2 * w.m;
-        v[h] = arc ? (int16_t)label : kInf;
+          label = 10 * __popc(pk[e + h].a) + 5 * __popc(pk[e + h].b) -
+                  2 * newly_dominated(Masks{qv.x, qv.y, qv.z, qv.w}, pk[e + h]) + 2 * w.m;
+        v[h] = (uint32_t)(uint16_t)((bad == 0) ? (int16_t)label : kInf);
       }
-      packed[e / 2] = (uint32_t)(uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
+      packed[e / 2] = v[0] | (v[1] << 16);
     }
-    *reinterpret_cast<uint4*>(A + q * lda + pc) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    *reinterpret_cast<uint4*>(dst) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
   }
+}
+
+// Rows per CTA of the builder's launch: the widest band (256, 128 or 64 rows) that still gives the GPU at
+// least three waves of CTAs (4 resident per SM), so the last wave's idle SMs cost little.
+int build_rows_per_cta(int64_t n, int64_t ctiles) {
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  for (int r = kBuildMaxRows; r > 64; r /= 2)
+    if (ctiles * ((n + r - 1) / r) >= 3 * 4 * (int64_t)sms) return r;
+  return 64;
 }
 
 }  // namespace
@@ -230,10 +278,11 @@ extern "C" rd_status rd_build_transfer(int m, int16_t* A_dev, int64_t lda, cudaS
   if (rd_state_count(m, &n) != RD_OK || !A_dev) return RD_ERR_ARG;
   if (lda < n || lda % 8 != 0 || !aligned16(A_dev)) return RD_ERR_ARG;
   const WordTable w = make_table(m);
-  const int64_t ptiles = (lda + kTp - 1) / kTp, qtiles = (n + kTq - 1) / kTq;
-  const int64_t tiles = ptiles * qtiles;
+  const int64_t ctiles = (lda + kBuildCols - 1) / kBuildCols;
+  const int rpc = build_rows_per_cta(n, ctiles);
+  const int64_t tiles = ctiles * ((n + rpc - 1) / rpc);
   if (tiles > 0x7FFFFFFF) return RD_ERR_ARG;
-  transfer_kernel<false><<<(unsigned)tiles, 256, 0, s>>>(w, n, A_dev, lda, ptiles);
+  transfer_kernel<false><<<(unsigned)tiles, kBuildThreads, 0, s>>>(w, n, A_dev, lda, ctiles, rpc);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
   return RD_OK;
@@ -244,10 +293,11 @@ extern "C" rd_status rd_build_transfer_loss(int m, int16_t* A_dev, int64_t lda, 
   if (m < 2 || rd_state_count(m, &n) != RD_OK || !A_dev) return RD_ERR_ARG;
   if (lda < n || lda % 8 != 0 || !aligned16(A_dev)) return RD_ERR_ARG;
   const WordTable w = make_table(m);
-  const int64_t ptiles = (lda + kTp - 1) / kTp, qtiles = (n + kTq - 1) / kTq;
-  const int64_t tiles = ptiles * qtiles;
+  const int64_t ctiles = (lda + kBuildCols - 1) / kBuildCols;
+  const int rpc = build_rows_per_cta(n, ctiles);
+  const int64_t tiles = ctiles * ((n + rpc - 1) / rpc);
   if (tiles > 0x7FFFFFFF) return RD_ERR_ARG;
-  transfer_kernel<true><<<(unsigned)tiles, 256, 0, s>>>(w, n, A_dev, lda, ptiles);
+  transfer_kernel<true><<<(unsigned)tiles, kBuildThreads, 0, s>>>(w, n, A_dev, lda, ctiles, rpc);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
   return RD_OK;
