@@ -503,7 +503,11 @@ def batched_products(rd, torch, count: int = 64, seed: int = 4) -> dict:
         return rd.power_until_periodic_sparse(A, n, plan, kmax, w)
 
     timings = {}
-    for name in ("sequential", "together_graph"):
+    for name in ("sequential", "together_graph", "together_graph_launches_per_phase"):
+        # the multi-run search advances all runs one power per launch of its step kernel; the third
+        # variant runs the same steps as launches per phase (products, normaliser, finalize, compare)
+        if name.endswith("per_phase"):
+            os.environ["RD_MULTI_STEP"] = "launches"
         for _ in range(2):  # first pass untimed
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -513,10 +517,14 @@ def batched_products(rd, torch, count: int = 64, seed: int = 4) -> dict:
                 res = rd.power_until_periodic_multi(runs, R, kmax, graph_steps=8)
             torch.cuda.synchronize()
             timings[name] = time.perf_counter() - t0
+        os.environ.pop("RD_MULTI_STEP", None)
         timings[name + "_triples"] = [(r["k"], r["p"], r["q"]) for r in res]
     out["periods_m1_to_9"] = {"sequential_s": timings["sequential"], "together_graph_s": timings["together_graph"],
+                              "together_launches_per_phase_s": timings["together_graph_launches_per_phase"],
                               "speedup": timings["sequential"] / timings["together_graph"],
-                              "same_results": timings["sequential_triples"] == timings["together_graph_triples"],
+                              "launches_per_step": 1,
+                              "same_results": (timings["sequential_triples"] == timings["together_graph_triples"] ==
+                                               timings["together_graph_launches_per_phase_triples"]),
                               "triples": timings["together_graph_triples"]}
     del runs
     torch.cuda.empty_cache()

@@ -421,12 +421,20 @@ rd_status rd_power_until_periodic_split(const int16_t *A_dev, int64_t lda, const
  * work buffer (rd_power_work_bytes) and its own outputs, with the meaning of
  * rd_power_until_periodic_sparse; `status` receives that call's status for the
  * run.  A run may instead carry a row-split plan (split_* fields), for the step
- * of rd_power_until_periodic_split.  One step of all runs is four launches (a
- * product over every sparse run's CTAs -- plus two per row-split run and one
- * per sparse run of N >= 4096 -- then normaliser/hash, finalize and compare side by side); stopped runs
- * exit at kernel entry.  graph_steps > 0 captures that many steps into one CUDA
- * graph (on a private stream ordered after s) and replays it until every run
- * has stopped; 0 launches the steps directly.  Returns RD_OK when the batch ran
+ * of rd_power_until_periodic_split.  The runs advance in groups, each on a
+ * stream of its own (forked from a private stream ordered after s, joined back
+ * after each block of steps), so the groups' steps run concurrently:
+ *  - all sparse-step runs form one group whose step is ONE launch of a
+ *    persistent kernel (R = 1 or 2; other R use one launch per phase) walking a
+ *    list of work items of every run -- product tiles, normaliser parts, a
+ *    finalize item, compare parts -- in that dependency order per run, each
+ *    dependency a wait bounded by time (about a second; past it the run stops
+ *    with RD_ERR_TIMEOUT);
+ *  - each row-split run is a group of its own, stepped by its two pass
+ *    launches, then finalize and compare.
+ * Stopped runs exit at kernel entry.  graph_steps > 0 captures that many steps
+ * of every group into one CUDA graph and replays it until every run has
+ * stopped; 0 enqueues the steps directly.  Returns RD_OK when the batch ran
  * (per-run results in runs[i].status), RD_ERR_ARG / RD_ERR_NOMEM / RD_ERR_CUDA
  * otherwise.  Synchronous.
  */

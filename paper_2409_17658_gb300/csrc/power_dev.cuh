@@ -1,7 +1,10 @@
 // power_dev.cuh -- device bodies of the power-step kernels (normaliser / hash,
 // finalize, exact compare), shared by the single-run and the multi-run launchers.
-// Every body indexes its grid with blockIdx.x / gridDim.x only, so a multi-run
-// kernel can give each run its own blockIdx.y.
+// The striding bodies split their rows into `parts` parts and work on part `part`
+// (by default blockIdx.x of gridDim.x), so a multi-run kernel can give each run its
+// own blockIdx.y, and the multi-run step kernel can run the parts as work items.
+// Data another CTA may have written earlier in the same launch (the product, the
+// normalised power, the search state) is read through L2 (__ldcg, volatile).
 #pragma once
 
 #include "rd_internal.cuh"
@@ -78,6 +81,9 @@ __device__ __forceinline__ void init_state_body(PowerState* st, int kmax, int sl
     st->hacc = 0;
     st->range_bad = 0;
     st->slots = slots;
+    for (int l = 0; l < 4; ++l) st->lvl_done[l] = 0;
+    st->queue = 0;
+    st->exited = 0;
   }
   int64_t* off = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(st) + kStateHeader);
   int64_t* gam = off + (kmax + 1);
@@ -123,8 +129,10 @@ __device__ __forceinline__ void reduce_min_diag_body(const int16_t* __restrict__
 // and the range check that keeps int16 exact.  Blocks stride over rows, threads over chunks.
 template <bool COPY>
 __device__ __forceinline__ void normalise_hash_body(const int16_t* __restrict__ src, PowerState* st, int16_t* ring,
-                                                    int64_t slot_elems, int slots, int64_t N, int64_t ld) {
+                                                    int64_t slot_elems, int slots, int64_t N, int64_t ld,
+                                                    int64_t part = -1, int64_t parts = -1) {
   __shared__ unsigned long long shh[kRedThreads / 32];
+  const int64_t b0 = part < 0 ? (int64_t)blockIdx.x : part, nb = parts < 0 ? (int64_t)gridDim.x : parts;
   if (*(volatile const int32_t*)&st->done) return;
   const int kn = *(volatile const int32_t*)&st->k + 1;
   int16_t* dst = ring + (int64_t)(kn % slots) * slot_elems;
@@ -134,10 +142,10 @@ __device__ __forceinline__ void normalise_hash_body(const int16_t* __restrict__ 
   const int64_t cpr = (N + 7) / 8;
   unsigned long long h = 0;
   int bad = 0;
-  for (int64_t i = blockIdx.x; i < N; i += gridDim.x) {
+  for (int64_t i = b0; i < N; i += nb) {
     for (int64_t c = threadIdx.x; c < cpr; c += blockDim.x) {
       const int64_t j0 = c * 8;
-      const uint4 v = *reinterpret_cast<const uint4*>(s + i * ld + j0);
+      const uint4 v = __ldcg(reinterpret_cast<const uint4*>(s + i * ld + j0));
       uint32_t w[4] = {v.x, v.y, v.z, v.w};
       const int64_t rem = N - j0;
       const int valid = rem < 8 ? (int)rem : 8;
@@ -168,24 +176,27 @@ __device__ __forceinline__ void normalise_hash_body(const int16_t* __restrict__ 
 
 // One warp: bookkeeping of power kn = k + 1 and the list of hash matches.
 __device__ __forceinline__ void finalize_body(PowerState* st) {
-  if (*(volatile const int32_t*)&st->done) return;
-  const int kn = st->k + 1;
+  volatile PowerState* vs = st;
+  if (vs->done) return;
+  const int kn = vs->k + 1;
   int64_t* off = st_offset(st);
   int64_t* gam = st_gamma(st);
   unsigned long long* hs = st_hash(st);
-  const unsigned long long hk = st->hacc;
+  const unsigned long long hk = vs->hacc;
+  const int32_t bad_range = vs->range_bad;
   if (threadIdx.x == 0) {
-    const int32_t mu = (st->mu >= kInf) ? 0 : st->mu;
+    const int32_t mu_raw = vs->mu, dmin = vs->dmin;
+    const int32_t mu = (mu_raw >= kInf) ? 0 : mu_raw;
     off[kn] = off[kn - 1] + mu;
-    gam[kn] = (st->dmin >= kInf) ? RD_GAMMA_INF : off[kn - 1] + st->dmin;
+    gam[kn] = (dmin >= kInf) ? RD_GAMMA_INF : off[kn - 1] + dmin;
     hs[kn] = hk;
-    if (st->range_bad) {
+    if (bad_range) {
       st->err |= kErrRange;
       st->done = 3;
     }
   }
   __syncwarp();
-  if (st->range_bad) return;
+  if (bad_range) return;
   for (int i = 1 + (int)threadIdx.x; i < kn; i += 32) {
     if (hs[i] != hk) continue;
     if (kn - i >= st->slots) {
@@ -200,23 +211,24 @@ __device__ __forceinline__ void finalize_body(PowerState* st) {
   if (threadIdx.x == 0 && st->err) st->done = 3;
 }
 
-// Exact comparison of P_kn with every candidate; the last CTA decides and advances k.
-__device__ __forceinline__ void compare_resolve_body(PowerState* st, int16_t* ring, int64_t slot_elems, int slots, int64_t N,
-                                       int64_t ld) {
+// Exact comparison of P_kn with every candidate; the last CTA (of `parts`) decides and advances k.
+__device__ __forceinline__ void compare_resolve_body(PowerState* st, int16_t* ring, int64_t slot_elems, int slots,
+                                                     int64_t N, int64_t ld, int64_t part = -1, int64_t parts = -1) {
   __shared__ int last;
+  const int64_t b0 = part < 0 ? (int64_t)blockIdx.x : part, nb = parts < 0 ? (int64_t)gridDim.x : parts;
   if (*(volatile const int32_t*)&st->done) return;
   const int kn = *(volatile const int32_t*)&st->k + 1;
   const int ncand = min(*(volatile const int32_t*)&st->ncand, kMaxCand);
   const int16_t* pk = ring + (int64_t)(kn % slots) * slot_elems;
   const int64_t cpr = (N + 7) / 8;
   for (int c = 0; c < ncand; ++c) {
-    const int16_t* pi = ring + (int64_t)(st->cand[c] % slots) * slot_elems;
+    const int16_t* pi = ring + (int64_t)(*(volatile const int32_t*)&st->cand[c] % slots) * slot_elems;
     int diff = 0;
-    for (int64_t i = blockIdx.x; i < N && !diff; i += gridDim.x) {
+    for (int64_t i = b0; i < N && !diff; i += nb) {
       for (int64_t cc = threadIdx.x; cc < cpr; cc += blockDim.x) {
         const int64_t j0 = cc * 8;
-        const uint4 a = *reinterpret_cast<const uint4*>(pk + i * ld + j0);
-        const uint4 b = *reinterpret_cast<const uint4*>(pi + i * ld + j0);
+        const uint4 a = __ldcg(reinterpret_cast<const uint4*>(pk + i * ld + j0));
+        const uint4 b = __ldcg(reinterpret_cast<const uint4*>(pi + i * ld + j0));
         uint32_t wa[4] = {a.x, a.y, a.z, a.w}, wb[4] = {b.x, b.y, b.z, b.w};
         const int64_t rem = N - j0;
         if (rem < 8) {
@@ -230,16 +242,16 @@ __device__ __forceinline__ void compare_resolve_body(PowerState* st, int16_t* ri
   }
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(&st->blocks_done, 1u) == gridDim.x - 1);
+  if (threadIdx.x == 0) last = (atomicAdd(&st->blocks_done, 1u) == (unsigned)(nb - 1));
   __syncthreads();
   if (!last || threadIdx.x != 0) return;
   __threadfence();
   int found = -1;
   for (int c = 0; c < ncand; ++c) {
-    const int i = st->cand[c];
+    const int i = *(volatile const int32_t*)&st->cand[c];
     if (!(*(volatile int32_t*)&st->mismatch[c]) && (found < 0 || i < found)) found = i;
   }
-  int64_t* off = st_offset(st);
+  volatile int64_t* off = st_offset(st);
   if (found >= 1) {
     st->found_i = found;
     st->found_j = kn;

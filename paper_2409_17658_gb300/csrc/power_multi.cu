@@ -1,13 +1,18 @@
 // power_multi.cu -- several period searches (Algorithm 2) advanced together.
 //
-// Each run is its own transfer matrix with its own work buffer (state + ring),
-// exactly as in rd_power_until_periodic_sparse.  A step of ALL runs is four
-// launches: the dense x sparse products (one launch over the concatenated CTA lists
-// of the small runs, one 2-D launch per large run), then the normaliser/hash,
-// finalize and compare of every run side by side (blockIdx.y = run).  Runs that have stopped exit at kernel entry, so the same
-// launch sequence stays valid until the last run stops; it is captured once
-// into a CUDA graph of several steps and replayed, so small matrices (m <= 5,
-// whose steps are launch-bound) ride along with the large ones at no cost.
+// Each run is its own transfer matrix with its own work buffer (state + ring), exactly as in
+// rd_power_until_periodic_sparse / _split.  The runs form groups that advance side by side:
+//  * every run stepped by the sparse step belongs to one group whose step is ONE launch of
+//    multi_step_kernel, a persistent kernel that walks a list of work items of all its runs in
+//    dependency levels (products, normaliser, finalize, compare; see below);
+//  * every run stepped by the row split is a group of its own, stepped by its two pass launches and
+//    its finalize and compare launches (inside the shared kernel its passes ran 40 % slower: one register
+//    budget and one code image for every kind of item).
+// rd_power_until_periodic_multi gives each group a stream of its own, forked from the caller's and joined
+// after a block of steps, and captures a block of steps of all groups into one CUDA graph, so the groups'
+// chains of steps run concurrently and small runs fill the gaps of the large ones.  Runs that have
+// stopped exit at kernel entry, so the same launch sequence stays valid until the last run stops.
+#include <cstdlib>
 #include <cstring>
 
 #include "power_dev.cuh"
@@ -152,7 +157,8 @@ cudaError_t launch_multi_product(int R, const MultiParams& mp, cudaStream_t s) {
   }
 }
 
-cudaError_t enqueue_multi_step(int R, const MultiParams& mp, int grid, cudaStream_t s) {
+// The step as launches per phase (products, normaliser, finalize, compare) for the runs of mp.
+cudaError_t enqueue_phase_step(int R, const MultiParams& mp, int grid, cudaStream_t s) {
   cudaError_t e = launch_multi_product(R, mp, s);
   if (e != cudaSuccess) return e;
   const dim3 g((unsigned)grid, (unsigned)mp.count);
@@ -160,6 +166,261 @@ cudaError_t enqueue_multi_step(int R, const MultiParams& mp, int grid, cudaStrea
   multi_finalize_kernel<<<dim3(1, (unsigned)mp.count), 32, 0, s>>>(mp);
   multi_compare_kernel<<<g, 256, 0, s>>>(mp);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- the sparse runs' step as one launch
+//
+// One launch of multi_step_kernel advances every sparse-step run of a group by one power.  Its work is a
+// list of items in four dependency levels per run:
+//   level 0  the product's (row block, slab) tiles, R = A (x) P_k with min and diagonal minimum;
+//   level 1  the normaliser's parts (P_(k+1) = R - mu, its hash and range flag);
+//   level 2  finalize: one item (offsets, gamma, hash table, candidates);
+//   level 3  the exact compare's parts; the last one advances k.
+// The list holds every run's level-0 items (largest run first), then level 1 (smallest first), then
+// levels 2 and 3.  CTAs take items in list order from a counter in the first run's state; an item waits
+// until its run's previous level has finished, a wait bounded by time (after about a second it marks its
+// run timed out and skips its work).  Every item an item waits for sits earlier in the list and was taken
+// by a running CTA that waits only for items earlier still, so the launch always progresses.  The last CTA
+// to leave clears the counters for the next launch.
+
+enum : int32_t { kItemSparse = 0, kItemNormalise = 1, kItemFinalize = 2, kItemCompare = 3 };
+constexpr int kStepThreads = 256;
+constexpr int kStepMaxSeg = 4 * kMaxRuns;
+constexpr long long kStepWaitCycles = 2000000000ll;  // about a second at GB300 clocks
+
+struct StepSeg {
+  int32_t run, kind;  // kind = the item's level
+  int64_t begin, count;
+};
+
+struct StepRun {
+  PowerState* st;
+  int16_t* ring;
+  int64_t slot_elems;
+  int32_t slots;
+  int64_t N, ld;
+  const int64_t* start;
+  const uint32_t* rec;
+  int64_t nb;         // row blocks of the product's tiles
+  int64_t parts;      // parts of the normaliser and of the compare
+  uint32_t need[4];   // items of each level
+};
+
+struct StepList {
+  int32_t count, nseg, R;
+  int64_t total;
+  StepSeg seg[kStepMaxSeg];
+  StepRun r[kMaxRuns];
+};
+
+// Thread 0 waits until level `lvl` of the run has `need` finished items; false when the bound ran out.
+__device__ __forceinline__ bool step_wait(PowerState* st, int lvl, uint32_t need) {
+  __shared__ int ok_sh;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const long long t0 = clock64();
+    while (*(volatile const uint32_t*)&st->lvl_done[lvl] < need) {
+      if (clock64() - t0 > kStepWaitCycles) {
+        ok = 0;
+        break;
+      }
+      __nanosleep(100);
+    }
+    __threadfence();
+    ok_sh = ok;
+  }
+  __syncthreads();
+  const int ok = ok_sh;
+  __syncthreads();
+  return ok != 0;
+}
+
+template <int R>
+__device__ __forceinline__ void step_sparse_item(const StepRun& q, int64_t local, uint32_t* srec) {
+  if (*(volatile const int32_t*)&q.st->done) return;
+  const int k = *(volatile const int32_t*)&q.st->k;
+  SparseArgs a{};
+  a.M = q.N;
+  a.start = q.start;
+  a.rec = q.rec;
+  a.ldb = q.ld;
+  a.ldc = q.ld;
+  a.Ncols = q.N;
+  a.min_out = &q.st->mu;
+  a.diag_out = &q.st->dmin;
+  const int16_t* B = q.ring + (int64_t)(k % q.slots) * q.slot_elems;
+  int16_t* C = q.ring + (int64_t)((k + 1) % q.slots) * q.slot_elems;
+  sparse_tile_body<R>(a, B, C, local % q.nb, local / q.nb, srec);
+}
+
+template <int R>
+__global__ void __launch_bounds__(kStepThreads) multi_step_kernel(const __grid_constant__ StepList L) {
+  __shared__ __align__(16) uint32_t srec[kChunk * record_words(R)];
+  __shared__ int64_t item_sh;
+  PowerState* st0 = L.r[0].st;
+  for (;;) {
+    if (threadIdx.x == 0) item_sh = (int64_t)atomicAdd(&st0->queue, 1u);
+    __syncthreads();
+    const int64_t it = item_sh;
+    __syncthreads();
+    if (it >= L.total) break;
+    int si = 0;
+    while (si + 1 < L.nseg && L.seg[si + 1].begin <= it) ++si;
+    const StepSeg& sg = L.seg[si];
+    const StepRun& q = L.r[sg.run];
+    const int64_t local = it - sg.begin;
+    const int lvl = sg.kind;
+    if (lvl > 0 && !step_wait(q.st, lvl - 1, q.need[lvl - 1])) {
+      if (threadIdx.x == 0) {
+        atomicOr(&q.st->err, kErrTimeout);
+        atomicExch(&q.st->done, 3);
+      }
+    } else {
+      switch (lvl) {
+        case kItemSparse: step_sparse_item<R>(q, local, srec); break;
+        case kItemNormalise:
+          normalise_hash_body<false>(nullptr, q.st, q.ring, q.slot_elems, q.slots, q.N, q.ld, local, q.parts);
+          break;
+        case kItemFinalize:
+          if (threadIdx.x < 32) finalize_body(q.st);
+          break;
+        default:
+          compare_resolve_body(q.st, q.ring, q.slot_elems, q.slots, q.N, q.ld, local, q.parts);
+          break;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&q.st->lvl_done[lvl], 1u);
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&st0->exited, 1u) == gridDim.x - 1) {
+      __threadfence();
+      for (int r = 0; r < L.count; ++r)
+        for (int l = 0; l < 4; ++l) L.r[r].st->lvl_done[l] = 0;
+      st0->queue = 0;
+      st0->exited = 0;
+      __threadfence();
+    }
+  }
+}
+
+// The step of the sparse-step runs of mp as one launch of multi_step_kernel with `ctas` CTAs (0: as many as
+// fit on the GPU); *used is false (nothing launched) when R is not 1 or 2 or mp holds a row-split run.
+cudaError_t launch_sparse_step(int R, const MultiParams& mp, int ctas, cudaStream_t s, bool* used) {
+  *used = false;
+  if (mp.count < 1 || !(R == 1 || R == 2)) return cudaSuccess;
+  for (int i = 0; i < mp.count; ++i)
+    if (mp.r[i].split != nullptr) return cudaSuccess;
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  StepList L{};
+  L.count = mp.count;
+  L.R = R;
+  for (int i = 0; i < mp.count; ++i) {
+    const MultiRun& d = mp.r[i];
+    StepRun& q = L.r[i];
+    q.st = d.st;
+    q.ring = d.ring;
+    q.slot_elems = d.slot_elems;
+    q.slots = d.slots;
+    q.N = d.N;
+    q.ld = d.ld;
+    q.start = d.start;
+    q.rec = d.rec;
+    q.nb = (d.N + R - 1) / R;
+    q.parts = d.N < 4 * (int64_t)sms ? d.N : 4 * (int64_t)sms;
+    const int64_t slabs = (d.N + kStepThreads * 16 - 1) / (kStepThreads * 16);
+    q.need[0] = (uint32_t)(q.nb * slabs);
+    q.need[1] = (uint32_t)q.parts;
+    q.need[2] = 1;
+    q.need[3] = (uint32_t)q.parts;
+  }
+  int order[kMaxRuns];
+  for (int i = 0; i < mp.count; ++i) order[i] = i;
+  for (int i = 1; i < mp.count; ++i)
+    for (int j = i; j > 0 && mp.r[order[j]].N > mp.r[order[j - 1]].N; --j) {
+      const int t = order[j];
+      order[j] = order[j - 1];
+      order[j - 1] = t;
+    }
+  int64_t at = 0;
+  auto add = [&](int run, int32_t kind, int64_t n) {
+    L.seg[L.nseg] = StepSeg{run, kind, at, n};
+    ++L.nseg;
+    at += n;
+  };
+  for (int o = 0; o < mp.count; ++o) add(order[o], kItemSparse, L.r[order[o]].need[0]);
+  for (int o = mp.count - 1; o >= 0; --o) add(order[o], kItemNormalise, L.r[order[o]].need[1]);
+  for (int i = 0; i < mp.count; ++i) add(i, kItemFinalize, 1);
+  for (int i = 0; i < mp.count; ++i) add(i, kItemCompare, L.r[i].need[3]);
+  L.total = at;
+  void (*k)(StepList) = (R == 1) ? multi_step_kernel<1> : multi_step_kernel<2>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kStepThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int grid = (ctas > 0 && ctas < per_sm * sms) ? ctas : per_sm * sms;
+  k<<<grid, kStepThreads, 0, s>>>(L);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) *used = true;
+  return e;
+}
+
+// The step as one launch per group where the group suits it, or when RD_MULTI_STEP=launches is set (to
+// compare the two forms), as launches per phase.
+bool one_launch_step_wanted() {
+  const char* v = getenv("RD_MULTI_STEP");
+  return !(v && strcmp(v, "launches") == 0);
+}
+
+cudaError_t enqueue_group_step(int R, const MultiParams& g, int grid, int ctas, cudaStream_t s) {
+  if (one_launch_step_wanted()) {
+    bool used = false;
+    const cudaError_t e = launch_sparse_step(R, g, ctas, s, &used);
+    if (e != cudaSuccess || used) return e;
+  }
+  return enqueue_phase_step(R, g, grid, s);
+}
+
+// A subset of the runs of mp as its own MultiParams.
+MultiParams subset(const MultiParams& mp, const int* idx, int n, int R) {
+  MultiParams g{};
+  g.count = n;
+  for (int i = 0; i < n; ++i) {
+    g.r[i] = mp.r[idx[i]];
+    const MultiRun& q = g.r[i];
+    (void)R;
+    if (q.N < kOwnLaunchN && q.split == nullptr) {
+      g.small[g.nsmall] = i;
+      g.cta_start[g.nsmall + 1] = g.cta_start[g.nsmall] + q.nb * q.slabs;
+      ++g.nsmall;
+    }
+  }
+  return g;
+}
+
+// The runs as groups: all sparse-step runs together (first, when there are any), each row-split run alone.
+int make_groups(const MultiParams& mp, int R, MultiParams* groups) {
+  int sparse_idx[kMaxRuns], ns = 0, ng = 0;
+  for (int i = 0; i < mp.count; ++i)
+    if (mp.r[i].split == nullptr) sparse_idx[ns++] = i;
+  if (ns > 0) groups[ng++] = subset(mp, sparse_idx, ns, R);
+  for (int i = 0; i < mp.count; ++i)
+    if (mp.r[i].split != nullptr) groups[ng++] = subset(mp, &i, 1, R);
+  return ng;
+}
+
+// One step of every run on one stream: the row-split runs' launches, then the sparse runs' one launch.
+cudaError_t enqueue_multi_step(int R, const MultiParams& mp, int grid, cudaStream_t s) {
+  MultiParams groups[kMaxRuns];
+  const int ng = make_groups(mp, R, groups);
+  cudaError_t e = cudaSuccess;
+  for (int gi = ng - 1; gi >= 0 && e == cudaSuccess; --gi) e = enqueue_group_step(R, groups[gi], grid, 0, s);
+  return e;
 }
 
 cudaError_t enqueue_multi_first(const MultiParams& mp, int kmax, int grid, cudaStream_t s) {
@@ -285,29 +546,57 @@ extern "C" rd_status rd_power_until_periodic_multi(rd_power_run* runs, int count
   int dev = 0, sms = 148;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = sms * 4;  // blocks per run for the streaming kernels, as in the single-run path
+  MultiParams groups[kMaxRuns];
+  const int ng = make_groups(mp, R, groups);
+  // the sparse runs' one-launch step shares the GPU with row-split groups: two CTAs per SM then, so their
+  // waits between levels hold few of the slots the row-split passes use (m = 1..9 on GB300: 8, 19, 38, 76,
+  // 152, 304 and 608 CTAs took 132, 69, 45.8, 43.9, 43.4, 42.7 and 43.3 ms)
+  const int sparse_ctas = ng > 1 ? 2 * sms : 0;
 
-  // Graph capture needs a stream other than the legacy default one: use a private stream
-  // ordered after `s` by events, and order `s` after it at the end.
+  // Graph capture needs a stream other than the legacy default one: a private stream w ordered after `s`
+  // by events (and `s` after it at the end), and one stream per group forked from w and joined back to it
+  // after each block of steps.
   cudaStream_t w = nullptr;
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaStream_t br[kMaxRuns] = {};
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr;
+  cudaEvent_t ev_join[kMaxRuns] = {};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&w, cudaStreamNonBlocking);
+  for (int g = 0; g < ng && e == cudaSuccess; ++g) {
+    e = cudaStreamCreateWithFlags(&br[g], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_join[g], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(ev_in, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(w, ev_in, 0);
   if (e == cudaSuccess) e = enqueue_multi_first(mp, kmax, grid, w);
+  // `steps` steps of every group, each group's chain on its own stream between a fork from w and a join to w
+  auto enqueue_block = [&](int steps) {
+    cudaError_t x = cudaEventRecord(ev_fork, w);
+    for (int g = 0; g < ng && x == cudaSuccess; ++g) {
+      x = cudaStreamWaitEvent(br[g], ev_fork, 0);
+      for (int i = 0; i < steps && x == cudaSuccess; ++i)
+        x = enqueue_group_step(R, groups[g], grid, groups[g].r[0].split ? 0 : sparse_ctas, br[g]);
+      if (x == cudaSuccess) x = cudaEventRecord(ev_join[g], br[g]);
+      if (x == cudaSuccess) x = cudaStreamWaitEvent(w, ev_join[g], 0);
+    }
+    return x;
+  };
   if (e == cudaSuccess && graph_steps > 0) {
     e = cudaStreamBeginCapture(w, cudaStreamCaptureModeThreadLocal);
-    for (int i = 0; i < graph_steps && e == cudaSuccess; ++i) e = enqueue_multi_step(R, mp, grid, w);
-    cudaGraph_t g = nullptr;
-    const cudaError_t e2 = cudaStreamEndCapture(w, &g);
-    if (e == cudaSuccess) e = e2;
-    graph = g;
+    if (e == cudaSuccess) {
+      e = enqueue_block(graph_steps);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(w, &g);
+      if (e == cudaSuccess) e = e2;
+      graph = g;
+    }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
   }
-  // Host loop: replay (or launch) steps until every run has stopped.
+  // Host loop: replay (or enqueue) blocks of steps until every run has stopped.
   const int per_check = graph_steps > 0 ? graph_steps : ((maxN >= 2048) ? 1 : 8);
   PowerState h[kMaxRuns];
   int enqueued = 1;
@@ -319,11 +608,7 @@ extern "C" rd_status rd_power_until_periodic_multi(rd_power_run* runs, int count
     bool all_done = true;
     for (int i = 0; i < count; ++i) all_done = all_done && (h[i].done != 0);
     if (all_done || enqueued >= kmax) break;
-    if (exec) {
-      e = cudaGraphLaunch(exec, w);
-    } else {
-      for (int i = 0; i < per_check && e == cudaSuccess; ++i) e = enqueue_multi_step(R, mp, grid, w);
-    }
+    e = exec ? cudaGraphLaunch(exec, w) : enqueue_block(per_check);
     enqueued += per_check;
   }
   rd_status rc = RD_OK;
@@ -359,6 +644,11 @@ extern "C" rd_status rd_power_until_periodic_multi(rd_power_run* runs, int count
   if (graph) cudaGraphDestroy(graph);
   if (ev_in) cudaEventDestroy(ev_in);
   if (ev_out) cudaEventDestroy(ev_out);
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  for (int g = 0; g < ng; ++g) {
+    if (ev_join[g]) cudaEventDestroy(ev_join[g]);
+    if (br[g]) cudaStreamDestroy(br[g]);
+  }
   if (w) cudaStreamDestroy(w);
   return rc;
 }

@@ -32,6 +32,11 @@ struct PowerState {
   unsigned long long hacc;  // hash accumulator of the power being normalised
   int32_t range_bad;
   int32_t slots;
+  // the multi-run step kernel: items finished per dependency level of this run in the current launch, and
+  // (in the first run's state) the launch's item queue and its count of CTAs that have left the queue
+  uint32_t lvl_done[4];
+  uint32_t queue;
+  uint32_t exited;
 };
 
 constexpr size_t kStateHeader = 256;

@@ -49,12 +49,13 @@ constexpr int kChunk = 128;  // entry records staged in shared memory at a time
 // One CTA = one block b of R rows x a slab of 16 * blockDim.x columns of C = A (x) B.
 // Thread t owns columns [base + 8t, base + 8t + 8) and [base + 8(T + t), base + 8(T + t) + 8),
 // so each of its two loads per B row is part of one contiguous warp-wide sweep.
+// srec: kChunk * record_words(R) words of shared memory for the staged entry records.
 template <int R>
 __device__ __forceinline__ void sparse_tile_body(const SparseArgs& a, const int16_t* __restrict__ B,
-                                                 int16_t* __restrict__ C, const int64_t b, const int64_t slab) {
+                                                 int16_t* __restrict__ C, const int64_t b, const int64_t slab,
+                                                 uint32_t* __restrict__ srec) {
   constexpr int W = record_words(R);
   constexpr int U = (R >= 8) ? 2 : 4;  // entries whose B rows are in flight together
-  __shared__ __align__(16) uint32_t srec[kChunk * W];
   const int T = blockDim.x;
   const int64_t base = slab * T * 16;
   const int64_t col[2] = {base + threadIdx.x * 8, base + (T + threadIdx.x) * 8};
@@ -162,6 +163,13 @@ __device__ __forceinline__ void sparse_tile_body(const SparseArgs& a, const int1
 }
 
 
+
+template <int R>
+__device__ __forceinline__ void sparse_tile_body(const SparseArgs& a, const int16_t* __restrict__ B,
+                                                 int16_t* __restrict__ C, const int64_t b, const int64_t slab) {
+  __shared__ __align__(16) uint32_t srec[kChunk * record_words(R)];
+  sparse_tile_body<R>(a, B, C, b, slab, srec);
+}
 
 // ---------------------------------------------------------------- the same tile fed by bulk copies
 //

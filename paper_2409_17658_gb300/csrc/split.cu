@@ -648,9 +648,11 @@ __host__ __device__ inline PassSmem pass_smem_layout(int max_slots, int n_groups
   return p;
 }
 
+// One (fiber f, slab group) of a pass: the body of split_pass_kernel, also run as an item of the multi-run
+// step kernel.  sm: the dynamic shared memory (pass_smem bytes).
 template <int W, bool FIRST, bool RING, bool STAGED>
-__global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 4) split_pass_kernel(SplitPass a) {
-  extern __shared__ uint4 sm[];
+__device__ __forceinline__ void split_pass_body(const SplitPass& a, const int64_t f, const int64_t slab_group,
+                                                uint4* sm) {
   constexpr int LR = W / 8;              // threads per row of the slab
   constexpr int G = kSplitThreads / LR;  // groups (resp. staged rows) handled side by side
   const int16_t* in = a.in;
@@ -666,8 +668,6 @@ __global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 4) split_pass_kerne
   in += a.in_col0;
   out += a.out_col0;
   const int lane = threadIdx.x % LR, gi = threadIdx.x / LR;
-  const int64_t f = a.fiber_x ? blockIdx.x : blockIdx.y;
-  const int64_t slab_group = a.fiber_x ? blockIdx.y : blockIdx.x;
   const uint4 inf4 = make_uint4(kInf2, kInf2, kInf2, kInf2);
 
   // stage the fiber's metadata once: sub-list bounds relative to the fiber's first list entry,
@@ -834,9 +834,14 @@ __global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 4) split_pass_kerne
     }
   }
 
+  // the block reductions below use the start of the staged-row buffer, dead once every warp has folded the
+  // last slab
+  __syncthreads();
+  unsigned long long* red_h = reinterpret_cast<unsigned long long*>(sm);
+  int32_t* red_v = reinterpret_cast<int32_t*>(red_h + kSplitThreads / 32);
+  int32_t* red_m = red_v + kSplitThreads / 32;
+  int32_t* red_d = red_m + kSplitThreads / 32;
   if (RING && a.norm) {
-    __shared__ unsigned long long red_h[kSplitThreads / 32];
-    __shared__ int32_t red_v[kSplitThreads / 32];
     if (FIRST) {
       int32_t v = (int32_t)min(mv & 0xFFFFu, mv >> 16);
       for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
@@ -868,7 +873,6 @@ __global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 4) split_pass_kerne
       lmin = min(lmin, __shfl_xor_sync(0xFFFFFFFFu, lmin, o));
       ldiag = min(ldiag, __shfl_xor_sync(0xFFFFFFFFu, ldiag, o));
     }
-    __shared__ int32_t red_m[kSplitThreads / 32], red_d[kSplitThreads / 32];
     const int warp = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
       red_m[warp] = lmin;
@@ -885,6 +889,14 @@ __global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 4) split_pass_kerne
       if (a.diag_out != nullptr && bd < *(volatile const int32_t*)a.diag_out) atomicMin(a.diag_out, bd);
     }
   }
+}
+
+template <int W, bool FIRST, bool RING, bool STAGED>
+__global__ void __launch_bounds__(kSplitThreads, FIRST ? 5 : 4) split_pass_kernel(SplitPass a) {
+  extern __shared__ uint4 sm[];
+  const int64_t f = a.fiber_x ? blockIdx.x : blockIdx.y;
+  const int64_t slab_group = a.fiber_x ? blockIdx.y : blockIdx.x;
+  split_pass_body<W, FIRST, RING, STAGED>(a, f, slab_group, sm);
 }
 
 constexpr size_t kSmemLimit = 220 * 1024;

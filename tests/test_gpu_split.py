@@ -312,6 +312,9 @@ def test_power_multi_mixes_split_and_sparse_runs(rd, torch_mod, orc, graph_steps
             assert n0 >= r["k"] and alpha % r["p"] == 0 and beta == r["q"] * (alpha // r["p"]), m
     for nn in range(3, 8):
         assert res[8]["gamma"][nn] == orc.row_dp(9, nn)
+    o9 = oracle_m9()
+    assert (res[8]["k"], res[8]["p"], res[8]["q"]) == (o9["k"], o9["p"], o9["q"])
+    assert [int(x) for x in res[8]["gamma"][1:res[8]["j"] + 1]] == o9["gamma"][1:o9["j"] + 1]
 
 
 @pytest.mark.parametrize("j", [1, 2, 5, 6])
