@@ -278,9 +278,34 @@ rd_status search_outputs(const PowerState& h, void* work_dev, int kmax, int64_t*
 
 // Algorithm 2 on a validated work area: state header, then the ring of powers.
 // No host heap use: the gamma table is copied straight into gamma_host.
+namespace {
+// Per host thread and device: two page-locked copies of the search state and their events, for the checks
+// of power_search (made on first use; host memory, not device memory).
+struct HostCheck {
+  PowerState* st = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  bool tried = false, ok = false;
+};
+constexpr int kCheckDevices = 16;
+HostCheck* host_check() {
+  thread_local HostCheck hc[kCheckDevices];
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kCheckDevices) return nullptr;
+  HostCheck& h = hc[dev];
+  if (!h.tried) {
+    h.tried = true;
+    cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&h.st), 2 * sizeof(PowerState), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h.ev[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h.ev[1], cudaEventDisableTiming);
+    h.ok = e == cudaSuccess;
+  }
+  return h.ok ? &h : nullptr;
+}
+}  // namespace
+
 rd_status power_search(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, void* work_dev, size_t work_bytes,
                        ProductFn product, const void* ctx, int64_t* gamma_host, int32_t* k_out, int32_t* p_out,
-                       int64_t* q_out, cudaStream_t s, bool normalised) {
+                       int64_t* q_out, cudaStream_t s, bool normalised, bool lookahead) {
   const size_t sb = state_bytes(kmax), pb = slot_bytes(N, lda);
   if (work_bytes < sb + 2 * pb) return RD_ERR_NOMEM;
   const size_t slots64 = (work_bytes - sb) / pb;
@@ -317,19 +342,50 @@ rd_status power_search(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, v
   // The row-split step (normalised) is about N / 100 times cheaper than the
   // dense one, so it batches up to larger N.
   const int chunk = normalised ? (N >= 16384 ? 1 : (N >= 4096 ? 4 : 8)) : (N >= 2048) ? 1 : (N >= 512 ? 4 : 16);
-  int enqueued = 1;
-  for (;;) {
-    e = cudaMemcpyAsync(&h, r.st, sizeof(PowerState), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return fail(e);
-    if (h.done || enqueued >= kmax) break;
-    const int n = (kmax - enqueued < chunk) ? (kmax - enqueued) : chunk;
-    for (int i = 0; i < n; ++i) {
-      e = enqueue_step(r, product, ctx, normalised, s);
+  int enqueued = 1, cur = 0;
+  HostCheck* hcp = lookahead ? host_check() : nullptr;
+  if (hcp == nullptr) {
+    // one block at a time: the host reads the state after each block before enqueuing the next
+    for (;;) {
+      e = cudaMemcpyAsync(&h, r.st, sizeof(PowerState), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return fail(e);
+      if (h.done || enqueued >= kmax) break;
+      const int n = (kmax - enqueued < chunk) ? (kmax - enqueued) : chunk;
+      for (int i = 0; i < n; ++i) {
+        e = enqueue_step(r, product, ctx, normalised, s);
+        if (e != cudaSuccess) return fail(e);
+      }
+      enqueued += n;
     }
-    enqueued += n;
+    return search_outputs(h, work_dev, kmax, gamma_host, k_out, p_out, q_out, s);
   }
+  // One block of steps stays queued ahead of the block the host is checking, so the GPU never waits for
+  // the host: the state after each block is copied to pinned host memory and an event marks it; steps
+  // enqueued after the relation was found exit at kernel entry.
+  HostCheck& hc = *hcp;
+  auto enqueue_block = [&](int slot) -> cudaError_t {
+    const int n = (kmax - enqueued < chunk) ? (kmax - enqueued) : chunk;
+    cudaError_t x = cudaSuccess;
+    for (int i = 0; i < n && x == cudaSuccess; ++i) x = enqueue_step(r, product, ctx, normalised, s);
+    enqueued += n;
+    if (x == cudaSuccess) x = cudaMemcpyAsync(&hc.st[slot], r.st, sizeof(PowerState), cudaMemcpyDeviceToHost, s);
+    if (x == cudaSuccess) x = cudaEventRecord(hc.ev[slot], s);
+    return x;
+  };
+  e = enqueue_block(cur);  // the first power's state, with the first block of steps
+  bool pending = e == cudaSuccess;
+  while (e == cudaSuccess && pending) {
+    const bool more = enqueued < kmax;
+    if (more) e = enqueue_block(1 - cur);
+    if (e == cudaSuccess) e = cudaEventSynchronize(hc.ev[cur]);
+    if (e != cudaSuccess) break;
+    h = hc.st[cur];
+    if (h.done) break;
+    pending = more;
+    cur = 1 - cur;
+  }
+  if (e != cudaSuccess) return fail(e);
   return search_outputs(h, work_dev, kmax, gamma_host, k_out, p_out, q_out, s);
 }
 

@@ -22,13 +22,17 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
 }
 
 // Hash of the 16-byte chunk of row i starting at column j0 (8 entries, entries past
-// the last column already replaced by RD_INF); the matrix hash is the wrapping sum
-// over all chunks, so it does not depend on the order of the reduction.
+// the last column already replaced by RD_INF): the NH sum of UMAC (Black, Halevi,
+// Krawczyk, Krovetz and Rogaway, 1999) over its four 32-bit words,
+// (w0 + k0)(w1 + k1) + (w2 + k2)(w3 + k3) mod 2^64, with keys drawn from the chunk's
+// position by multiplicative hashing.  The matrix hash is the wrapping sum over all
+// chunks, so it does not depend on the order of the reduction; equal matrices hash
+// equal, and the hash only pre-filters the exact compare.
 __device__ __forceinline__ unsigned long long chunk_hash(int64_t i, int64_t j0, const uint32_t w[4]) {
-  const unsigned long long lo = (unsigned long long)w[0] | ((unsigned long long)w[1] << 32);
-  const unsigned long long hi = (unsigned long long)w[2] | ((unsigned long long)w[3] << 32);
-  const unsigned long long pos = ((unsigned long long)i << 32) ^ (unsigned long long)j0;
-  return mix64(pos ^ lo ^ (hi * 0x9E3779B97F4A7C15ull));
+  const uint32_t k0 = ((uint32_t)i * 0x9E3779B1u) ^ (((uint32_t)j0 >> 3) * 0x85EBCA77u);
+  const uint32_t k1 = k0 * 0xC2B2AE3Du, k2 = k0 ^ 0x27D4EB2Fu, k3 = k2 * 0x165667B1u;
+  return (unsigned long long)(w[0] + k0) * (unsigned long long)(w[1] + k1) +
+         (unsigned long long)(w[2] + k2) * (unsigned long long)(w[3] + k3);
 }
 
 // Lanes e >= valid of a chunk: RD_INF (their contents are padding and must not matter).

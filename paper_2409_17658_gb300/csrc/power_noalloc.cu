@@ -57,5 +57,5 @@ extern "C" rd_status rd_power_until_periodic_noalloc(const int16_t* A_dev, int64
   const rd_status rc = scratch_address(&scratch);
   if (rc != RD_OK) return rc;
   return rd::power_search(A_dev, N, lda, kmax, scratch, (size_t)RD_NOALLOC_SCRATCH_BYTES, rd::dense_power_product,
-                          nullptr, gamma_host, k_out, p_out, q_out, s);
+                          nullptr, gamma_host, k_out, p_out, q_out, s, false, false);
 }

@@ -118,10 +118,12 @@ typedef cudaError_t (*ProductFn)(const Run& r, const void* ctx, cudaStream_t s);
 cudaError_t dense_power_product(const Run& r, const void* ctx, cudaStream_t s);
 
 // `normalised`: the product itself writes the normalised power, its hash and range flag into the
-// state (the row-split step), so the normaliser pass is skipped.
+// state (the row-split step), so the normaliser pass is skipped.  `lookahead`: keep a block of steps
+// queued ahead of the host's check (uses page-locked host memory, made once per thread and device);
+// false reads the state after each block with no allocation at all.
 rd_status power_search(const int16_t* A_dev, int64_t N, int64_t lda, int kmax, void* work_dev, size_t work_bytes,
                        ProductFn product, const void* ctx, int64_t* gamma_host, int32_t* k_out, int32_t* p_out,
-                       int64_t* q_out, cudaStream_t s, bool normalised = false);
+                       int64_t* q_out, cudaStream_t s, bool normalised = false, bool lookahead = true);
 
 // A built row-split plan with its intermediate (split.cu), and the ring-mode product it runs: the
 // next power A(G) (x) P_k, already normalised, into the slot of power st->k + 1, with its minimum
