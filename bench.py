@@ -694,6 +694,8 @@ def main() -> None:
     ap.add_argument("--batched-only", action="store_true", help="time only the 64-product batch (profiling aid)")
     ap.add_argument("--build-only", type=int, default=0, metavar="M",
                     help="time only the A(G) builder at m = M (profiling aid)")
+    ap.add_argument("--multi-only", type=int, default=0, metavar="M",
+                    help="time only the period searches of m = 1..M advanced together (profiling aid)")
     ap.add_argument("--tune-table", default="", metavar="PATH",
                     help="load a saved tuning table (JSON, paper_2409_17658_gb300.tuning) before running")
     ap.add_argument("--no-sweep", action="store_true", help="skip the dense sweep at the other sizes")
@@ -719,6 +721,23 @@ def main() -> None:
         return run_split_only(rd, torch, args)
     if args.batched_only:
         return run_batched_only(rd, torch, args)
+    if args.multi_only:
+        kmax, R = 64, 2
+        runs = []
+        for m in range(1, args.multi_only + 1):
+            A, n = rd.transfer_matrix(m)
+            plan = rd.split_plan(m, x_ld=A.stride(0)) if m >= 8 else rd.sparse_plan(A, n, n, R)
+            runs.append((A, n, plan, rd.power_workspace(n, A.stride(0), kmax, 8)))
+        for _ in range(max(args.warmup, 1)):
+            rd.power_until_periodic_multi(runs, R, kmax, graph_steps=8)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            res = rd.power_until_periodic_multi(runs, R, kmax, graph_steps=8)
+        torch.cuda.synchronize()
+        print(json.dumps({"multi_only": args.multi_only, "s_per_search": (time.perf_counter() - t0) / args.steps,
+                          "triples": [(r["k"], r["p"], r["q"]) for r in res]}))
+        return
     if args.build_only:
         m = args.build_only
         n = rd.state_count(m)
