@@ -464,6 +464,21 @@ rd_status rd_power_until_periodic_multi(rd_power_run *runs, int count, int R, in
                                         cudaStream_t s);
 
 /*
+ * rd_power_until_periodic_multi_bounded -- rd_power_until_periodic_multi with
+ * the failure handling of its one-launch step exposed, so that the timeout path
+ * runs without faulting or hanging a GPU: wait_ms (1..60000) bounds every wait
+ * of an item for its run's previous level (rd_power_until_periodic_multi uses
+ * 1000), and stall_run (-1: none) makes that run's product level count one item
+ * more than it has, as a lost item would, so its normaliser items wait until
+ * the bound runs out.  That run then stops with status RD_ERR_TIMEOUT; its
+ * later items do no work and wait for nothing, and every other run's search
+ * and results are unaffected.  Only runs of the sparse step can be stalled (a
+ * row-split stall_run is ignored).
+ */
+rd_status rd_power_until_periodic_multi_bounded(rd_power_run *runs, int count, int R, int kmax, int graph_steps,
+                                                uint32_t wait_ms, int32_t stall_run, cudaStream_t s);
+
+/*
  * Query server with continuous batching (for many gamma_R(P_m box C_n) queries).
  * A worker thread on the device current at creation keeps one period-search job
  * per m that has been asked for and is not settled yet.  Each step advances all

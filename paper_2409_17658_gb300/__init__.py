@@ -57,6 +57,9 @@ def _lib():
         lib.rd_minplus_gemm_batched.argtypes = [vp, ctypes.c_int, vp]
         lib.rd_minplus_gemv.argtypes = [vp, vp, i64, vp, i64, i64, vp, vp]
         lib.rd_power_until_periodic_multi.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
+        lib.rd_power_until_periodic_multi_bounded.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                              ctypes.c_uint32, ctypes.c_int32, vp]
+        lib.rd_power_until_periodic_multi_bounded.restype = st
         lib.rd_server_create.argtypes = [sz, ctypes.c_int, vp]
         lib.rd_server_submit.argtypes = [vp, ctypes.c_int, vp, vp, vp]
         lib.rd_server_wait.argtypes = [vp, ctypes.c_int, vp, ctypes.c_double, vp, vp, vp]
@@ -235,9 +238,11 @@ class PowerRun(ctypes.Structure):
                 ("split_ldx", ctypes.c_int64)]
 
 
-def power_until_periodic_multi(runs, R: int, kmax: int, graph_steps: int = 8, stream=None) -> list:
+def power_until_periodic_multi(runs, R: int, kmax: int, graph_steps: int = 8, stream=None, wait_ms: int = 1000,
+                               stall_run: int = -1) -> list:
     """runs: list of (A, n, plan, work), plan from sparse_plan() (rows per block R) or split_plan().
-    All searches advance together; returns one result dict per run."""
+    All searches advance together; returns one result dict per run.  wait_ms and stall_run: see
+    rd_power_until_periodic_multi_bounded (the defaults are rd_power_until_periodic_multi)."""
     arr = (PowerRun * len(runs))()
     gammas = []
     for i, (A, n, plan, work) in enumerate(runs):
@@ -252,11 +257,14 @@ def power_until_periodic_multi(runs, R: int, kmax: int, graph_steps: int = 8, st
         assert plan["R"] == R
         arr[i] = PowerRun(A.data_ptr(), n, A.stride(0), plan["block_start"].data_ptr(), plan["records"].data_ptr(),
                           work.data_ptr(), work.numel() * work.element_size(), g.ctypes.data, 0, 0, 0, 0)
-    _check(_lib().rd_power_until_periodic_multi(arr, len(runs), R, kmax, graph_steps, _stream(stream)),
-           "rd_power_until_periodic_multi")
+    _check(_lib().rd_power_until_periodic_multi_bounded(arr, len(runs), R, kmax, graph_steps, wait_ms, stall_run,
+                                                        _stream(stream)), "rd_power_until_periodic_multi")
     out = []
     for i in range(len(runs)):
         st = arr[i].status
+        if i == stall_run:
+            out.append(dict(status=st, found=False, k=None, p=None, q=None, j=kmax, gamma=gammas[i]))
+            continue
         _check(st, f"rd_power_until_periodic_multi run {i}", ok=(RD_OK, RD_NOT_FOUND))
         found = st == RD_OK
         out.append(dict(status=st, found=found, k=arr[i].k if found else None, p=arr[i].p if found else None,

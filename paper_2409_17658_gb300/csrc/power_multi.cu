@@ -186,7 +186,7 @@ cudaError_t enqueue_phase_step(int R, const MultiParams& mp, int grid, cudaStrea
 enum : int32_t { kItemSparse = 0, kItemNormalise = 1, kItemFinalize = 2, kItemCompare = 3 };
 constexpr int kStepThreads = 256;
 constexpr int kStepMaxSeg = 4 * kMaxRuns;
-constexpr long long kStepWaitCycles = 2000000000ll;  // about a second at GB300 clocks
+constexpr uint64_t kStepWaitNs = 1000000000ull;  // the default bound of a wait: one second
 
 struct StepSeg {
   int32_t run, kind;  // kind = the item's level
@@ -209,18 +209,25 @@ struct StepRun {
 struct StepList {
   int32_t count, nseg, R;
   int64_t total;
+  uint64_t wait_ns;  // bound of a wait between levels
   StepSeg seg[kStepMaxSeg];
   StepRun r[kMaxRuns];
 };
 
-// Thread 0 waits until level `lvl` of the run has `need` finished items; false when the bound ran out.
-__device__ __forceinline__ bool step_wait(PowerState* st, int lvl, uint32_t need) {
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Thread 0 waits until level `lvl` of the run has `need` finished items; false when `wait_ns` ran out.
+__device__ __forceinline__ bool step_wait(PowerState* st, int lvl, uint32_t need, uint64_t wait_ns) {
   __shared__ int ok_sh;
   if (threadIdx.x == 0) {
     int ok = 1;
-    const long long t0 = clock64();
+    const uint64_t t0 = global_ns();
     while (*(volatile const uint32_t*)&st->lvl_done[lvl] < need) {
-      if (clock64() - t0 > kStepWaitCycles) {
+      if (global_ns() - t0 > wait_ns) {
         ok = 0;
         break;
       }
@@ -270,7 +277,9 @@ __global__ void __launch_bounds__(kStepThreads) multi_step_kernel(const __grid_c
     const StepRun& q = L.r[sg.run];
     const int64_t local = it - sg.begin;
     const int lvl = sg.kind;
-    if (lvl > 0 && !step_wait(q.st, lvl - 1, q.need[lvl - 1])) {
+    // a run that has stopped does no work, so its items need not wait
+    const bool stopped = *(volatile const int32_t*)&q.st->done != 0;
+    if (lvl > 0 && !stopped && !step_wait(q.st, lvl - 1, q.need[lvl - 1], L.wait_ns)) {
       if (threadIdx.x == 0) {
         atomicOr(&q.st->err, kErrTimeout);
         atomicExch(&q.st->done, 3);
@@ -310,7 +319,10 @@ __global__ void __launch_bounds__(kStepThreads) multi_step_kernel(const __grid_c
 
 // The step of the sparse-step runs of mp as one launch of multi_step_kernel with `ctas` CTAs (0: as many as
 // fit on the GPU); *used is false (nothing launched) when R is not 1 or 2 or mp holds a row-split run.
-cudaError_t launch_sparse_step(int R, const MultiParams& mp, int ctas, cudaStream_t s, bool* used) {
+// wait_ns bounds each wait between levels; stall >= 0 makes that run's level 0 count one item more than
+// it has, so its level-1 items wait until the bound runs out (the timeout path, exercised by a test).
+cudaError_t launch_sparse_step(int R, const MultiParams& mp, int ctas, uint64_t wait_ns, int stall, cudaStream_t s,
+                               bool* used) {
   *used = false;
   if (mp.count < 1 || !(R == 1 || R == 2)) return cudaSuccess;
   for (int i = 0; i < mp.count; ++i)
@@ -339,6 +351,7 @@ cudaError_t launch_sparse_step(int R, const MultiParams& mp, int ctas, cudaStrea
     q.need[2] = 1;
     q.need[3] = (uint32_t)q.parts;
   }
+  L.wait_ns = wait_ns;
   int order[kMaxRuns];
   for (int i = 0; i < mp.count; ++i) order[i] = i;
   for (int i = 1; i < mp.count; ++i)
@@ -358,6 +371,7 @@ cudaError_t launch_sparse_step(int R, const MultiParams& mp, int ctas, cudaStrea
   for (int i = 0; i < mp.count; ++i) add(i, kItemFinalize, 1);
   for (int i = 0; i < mp.count; ++i) add(i, kItemCompare, L.r[i].need[3]);
   L.total = at;
+  if (stall >= 0 && stall < mp.count) L.r[stall].need[0] += 1;
   void (*k)(StepList) = (R == 1) ? multi_step_kernel<1> : multi_step_kernel<2>;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kStepThreads, 0);
@@ -377,10 +391,11 @@ bool one_launch_step_wanted() {
   return !(v && strcmp(v, "launches") == 0);
 }
 
-cudaError_t enqueue_group_step(int R, const MultiParams& g, int grid, int ctas, cudaStream_t s) {
+cudaError_t enqueue_group_step(int R, const MultiParams& g, int grid, int ctas, cudaStream_t s,
+                               uint64_t wait_ns = kStepWaitNs, int stall = -1) {
   if (one_launch_step_wanted()) {
     bool used = false;
-    const cudaError_t e = launch_sparse_step(R, g, ctas, s, &used);
+    const cudaError_t e = launch_sparse_step(R, g, ctas, wait_ns, stall, s, &used);
     if (e != cudaSuccess || used) return e;
   }
   return enqueue_phase_step(R, g, grid, s);
@@ -495,9 +510,12 @@ cudaError_t runs_step(const RunDesc* runs, int count, int R, cudaStream_t s) {
 
 using namespace rd;
 
-extern "C" rd_status rd_power_until_periodic_multi(rd_power_run* runs, int count, int R, int kmax, int graph_steps,
-                                                   cudaStream_t s) {
+extern "C" rd_status rd_power_until_periodic_multi_bounded(rd_power_run* runs, int count, int R, int kmax,
+                                                           int graph_steps, uint32_t wait_ms, int32_t stall_run,
+                                                           cudaStream_t s) {
   if (!runs || count < 1 || count > kMaxRuns || kmax < 1 || kmax > (1 << 20) || graph_steps < 0) return RD_ERR_ARG;
+  if (wait_ms < 1 || wait_ms > 60000 || stall_run < -1 || stall_run >= count) return RD_ERR_ARG;
+  const uint64_t wait_ns = (uint64_t)wait_ms * 1000000ull;
   if (!(R == 1 || R == 2 || R == 4 || R == 8)) return RD_ERR_ARG;
   MultiParams mp{};
   mp.count = count;
@@ -548,6 +566,12 @@ extern "C" rd_status rd_power_until_periodic_multi(rd_power_run* runs, int count
   const int grid = sms * 4;  // blocks per run for the streaming kernels, as in the single-run path
   MultiParams groups[kMaxRuns];
   const int ng = make_groups(mp, R, groups);
+  // the stalled run's place in the sparse group (the group lists its runs in the order of runs[])
+  int stall_in_group = -1;
+  if (stall_run >= 0 && mp.r[stall_run].split == nullptr) {
+    stall_in_group = 0;
+    for (int i = 0; i < stall_run; ++i) stall_in_group += mp.r[i].split == nullptr ? 1 : 0;
+  }
   // the sparse runs' one-launch step shares the GPU with row-split groups: two CTAs per SM then, so their
   // waits between levels hold few of the slots the row-split passes use (m = 1..9 on GB300: 8, 19, 38, 76,
   // 152, 304 and 608 CTAs took 132, 69, 45.8, 43.9, 43.4, 42.7 and 43.3 ms)
@@ -579,7 +603,8 @@ extern "C" rd_status rd_power_until_periodic_multi(rd_power_run* runs, int count
     for (int g = 0; g < ng && x == cudaSuccess; ++g) {
       x = cudaStreamWaitEvent(br[g], ev_fork, 0);
       for (int i = 0; i < steps && x == cudaSuccess; ++i)
-        x = enqueue_group_step(R, groups[g], grid, groups[g].r[0].split ? 0 : sparse_ctas, br[g]);
+        x = enqueue_group_step(R, groups[g], grid, groups[g].r[0].split ? 0 : sparse_ctas, br[g], wait_ns,
+                               groups[g].r[0].split ? -1 : stall_in_group);
       if (x == cudaSuccess) x = cudaEventRecord(ev_join[g], br[g]);
       if (x == cudaSuccess) x = cudaStreamWaitEvent(w, ev_join[g], 0);
     }
@@ -651,4 +676,9 @@ extern "C" rd_status rd_power_until_periodic_multi(rd_power_run* runs, int count
   }
   if (w) cudaStreamDestroy(w);
   return rc;
+}
+
+extern "C" rd_status rd_power_until_periodic_multi(rd_power_run* runs, int count, int R, int kmax, int graph_steps,
+                                                   cudaStream_t s) {
+  return rd_power_until_periodic_multi_bounded(runs, count, R, kmax, graph_steps, 1000, -1, s);
 }

@@ -560,6 +560,41 @@ def test_power_multi_equals_single_runs(rd, torch_mod, orc, graph_steps):
     assert (res[8]["k"], res[8]["p"], res[8]["q"]) == (22, 5, 20)
 
 
+def test_power_multi_wait_runs_out(rd, torch_mod, orc):
+    """The one-launch step's bounded wait gives up and says so, and the GPU stays usable.  The run of m = 5 is
+    stalled: its product level counts one item more than it has, as a lost item would, so its normaliser
+    items wait until the bound (50 ms) runs out.  That run stops with RD_ERR_TIMEOUT; the other runs' relations
+    and gamma equal the oracle's; the next call without a stall is exact for every run."""
+    kmax = 48
+    ms = (3, 4, 5, 6, 7)
+    runs = []
+    for m in ms:
+        A, n = rd.transfer_matrix(m)
+        runs.append((A, n, rd.sparse_plan(A, n, n, 2), rd.power_workspace(n, A.stride(0), kmax, 8)))
+    want = {m: orc.power_until_periodic(m, kmax=kmax) for m in ms}
+    res = rd.power_until_periodic_multi(runs, 2, kmax, graph_steps=8, wait_ms=50, stall_run=2)
+    assert res[2]["status"] == rd.RD_ERR_TIMEOUT
+    for i, m in enumerate(ms):
+        if i == 2:
+            continue
+        o = want[m]
+        assert (res[i]["k"], res[i]["p"], res[i]["q"]) == (o["k"], o["p"], o["q"]), m
+        assert np.array_equal(res[i]["gamma"][1:o["j"] + 1], o["gamma"][1:o["j"] + 1]), m
+    res = rd.power_until_periodic_multi(runs, 2, kmax, graph_steps=8)
+    for i, m in enumerate(ms):
+        o = want[m]
+        assert (res[i]["k"], res[i]["p"], res[i]["q"]) == (o["k"], o["p"], o["q"]), m
+        assert np.array_equal(res[i]["gamma"][1:o["j"] + 1], o["gamma"][1:o["j"] + 1]), m
+
+
+def test_power_multi_bounded_rejects_bad_knobs(rd, torch_mod):
+    lib = rd._lib()
+    arr = (rd.PowerRun * 1)()
+    assert lib.rd_power_until_periodic_multi_bounded(arr, 1, 2, 8, 0, 0, -1, None) == rd.RD_ERR_ARG
+    assert lib.rd_power_until_periodic_multi_bounded(arr, 1, 2, 8, 0, 100, 1, None) == rd.RD_ERR_ARG
+    assert lib.rd_power_until_periodic_multi_bounded(arr, 1, 2, 8, 0, 100, -2, None) == rd.RD_ERR_ARG
+
+
 @pytest.mark.parametrize("R", [1, 2, 4, 8])
 @pytest.mark.parametrize("shape", SPARSE_SHAPES + [(300, 2000, 2500)])
 def test_sparse_minplus_tma(rd, torch_mod, orc, shape, R):
