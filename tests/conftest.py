@@ -27,16 +27,21 @@ def read_golden(name):
     return rows
 
 
-def oracle_m9():
-    """The oracle's m = 9 result (tests/golden/oracle_m9_first_repeat.txt, written by make_oracle_m9.py,
-    which calls only the oracle): dict(k, p, q, j, gamma) with gamma[n] for n = 1..len - 1."""
-    rows = read_golden("oracle_m9_first_repeat.txt")
-    m, k, p, q, j = map(int, rows[0])
-    assert m == 9
+def oracle_first_repeat(m):
+    """The oracle's stored result for m (tests/golden/oracle_m<m>_first_repeat.txt, written by
+    tests/golden/make_oracle_first_repeat.py, which calls only the oracle): dict(k, p, q, j, gamma) with
+    gamma[n] for n = 1..len - 1."""
+    rows = read_golden(f"oracle_m{m}_first_repeat.txt")
+    mm, k, p, q, j = map(int, rows[0])
+    assert mm == m
     gamma = [None] * (len(rows))
     for n, g in rows[1:]:
         gamma[int(n)] = int(g)
     return dict(k=k, p=p, q=q, j=j, gamma=gamma)
+
+
+def oracle_m9():
+    return oracle_first_repeat(9)
 
 
 @pytest.fixture(scope="session")
