@@ -214,7 +214,10 @@ rd_status rd_power_until_periodic(const int16_t *A_dev, int64_t N, int64_t lda, 
  * work_bytes).  On return from that call the last `slots` powers computed are
  * resident: P_k for last - slots < k <= last, where last = k_out + p_out when a
  * relation was found.  The matrix there is N x lda int16 with min entry 0;
- * A^k = o_k (x) P_k.  RD_ERR_ARG when k < 1 or the arguments describe no ring.
+ * A^k = o_k (x) P_k.  k = 0 gives the slot the search writes only from its
+ * second power on: a caller short of memory may build A itself there (A_dev
+ * then points into work_dev), since A is read only for the first power.
+ * RD_ERR_ARG when k < 0 or the arguments describe no ring.
  */
 rd_status rd_power_slot(int64_t N, int64_t lda, int kmax, size_t work_bytes, int k, size_t *byte_offset);
 
@@ -407,7 +410,15 @@ rd_status rd_split_minplus(const rd_split_info_t *info, const void *plan_dev, co
  * rd_power_until_periodic_split -- rd_power_until_periodic (same work buffer,
  * outputs and errors) for A = A(G) of the plan's m, with the power step
  * R = A (x) P_k run by the two passes of rd_split_minplus.  A_dev (N x N,
- * lda) is read once, for the first power; X_dev as in rd_split_minplus.
+ * lda) is read once, for the first power (it may sit in the ring slot of
+ * power 0, see rd_power_slot); X_dev as in rd_split_minplus.
+ * Short rings: when the only power whose hash matches the new power P_j has
+ * left the ring and the ring has at least 3 slots, the search stops at j,
+ * re-derives that power P_i from A(G) (rebuilt for the plan's m) in the two
+ * slots that do not hold P_j -- the same products and normalisation as the
+ * search -- and compares it with P_j entry by entry: equal gives the relation
+ * (k, p) = (i, j - i) and RD_OK; otherwise (a hash collision) RD_ERR_NOMEM.
+ * This lets m = 11 (73 GB per power) search with 3 slots.
  */
 rd_status rd_power_until_periodic_split(const int16_t *A_dev, int64_t lda, const rd_split_info_t *info,
                                         const void *plan_dev, int16_t *X_dev, int64_t ldx, int kmax, void *work_dev,

@@ -400,7 +400,7 @@ extern "C" rd_status rd_power_work_bytes(int64_t N, int64_t ld, int kmax, int sl
 }
 
 extern "C" rd_status rd_power_slot(int64_t N, int64_t ld, int kmax, size_t work_bytes, int k, size_t* byte_offset) {
-  if (N < 1 || ld < N || ld % 8 != 0 || kmax < 1 || k < 1 || k > kmax || !byte_offset) return RD_ERR_ARG;
+  if (N < 1 || ld < N || ld % 8 != 0 || kmax < 1 || k < 0 || k > kmax || !byte_offset) return RD_ERR_ARG;
   const size_t sb = state_bytes(kmax), pb = slot_bytes(N, ld);
   if (work_bytes < sb + 2 * pb) return RD_ERR_ARG;
   size_t slots = (work_bytes - sb) / pb;
@@ -449,10 +449,20 @@ rd_status compute_cached(int m, Cached* out) {
   int64_t N = 0, ld = 0;
   if (rd_state_count(m, &N) != RD_OK) return RD_ERR_ARG;
   rd_padded_dim(N, &ld);
-  const int slots = (N <= 8192) ? 16 : 8;
+  const int split_j = rd_split_default_j(m);
+  const size_t mat = (size_t)N * (size_t)ld * 2;
+  // Low-memory form when A(G), 8 ring slots and the whole intermediate of the row split do not fit (m >= 11:
+  // 73 GB per power): 3 ring slots with A(G) built in the first (it is read only for the first power), the
+  // intermediate in 8192-column chunks, and a repeat whose earlier power has left the ring verified by
+  // re-deriving that power (rd_power_until_periodic_split).
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const bool lowmem = split_j > 0 && N > 8192 && mat * 11 > free_b;
+  const int slots = lowmem ? 3 : (N <= 8192) ? 16 : 8;
   size_t wbytes = 0;
   rd_power_work_bytes(N, ld, kGammaKmax, slots, &wbytes);
   int16_t* A = nullptr;
+  int16_t* A_own = nullptr;
   void* work = nullptr;
   cudaStream_t s = nullptr;
   rd_status rc = RD_OK;
@@ -460,19 +470,24 @@ rd_status compute_cached(int m, Cached* out) {
   int32_t k = 0, p = 0;
   int64_t q = 0;
   cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMalloc(&A, (size_t)N * (size_t)ld * 2);
+  if (e == cudaSuccess && !lowmem) e = cudaMalloc(&A_own, mat);
   if (e == cudaSuccess) e = cudaMalloc(&work, wbytes);
   if (e != cudaSuccess) {
     set_cuda_error(e);
     rc = (e == cudaErrorMemoryAllocation) ? RD_ERR_NOMEM : RD_ERR_CUDA;
   }
+  A = A_own;
+  if (rc == RD_OK && lowmem) {
+    size_t off0 = 0;
+    rc = rd_power_slot(N, ld, kGammaKmax, wbytes, 0, &off0);
+    A = reinterpret_cast<int16_t*>(static_cast<char*>(work) + off0);
+  }
   if (rc == RD_OK) rc = rd_build_transfer(m, A, ld, s);
-  const int split_j = rd_split_default_j(m);
   if (rc == RD_OK && N <= kSmallN) {
     // small matrices: the whole search in one CTA
     rc = rd_power_until_periodic(A, N, ld, kGammaKmax, work, wbytes, g.data(), &k, &p, &q, s);
     if (s) cudaStreamSynchronize(s);
-    if (A) cudaFree(A);
+    if (A_own) cudaFree(A_own);
     if (work) cudaFree(work);
     if (s) cudaStreamDestroy(s);
     return finish_cached(rc, g, k, p, q, out);
@@ -486,17 +501,19 @@ rd_status compute_cached(int m, Cached* out) {
     rc = rd_split_plan_bytes(m, split_j, &pbytes);
     if (rc == RD_OK) e = cudaMalloc(&plan, pbytes);
     if (rc == RD_OK && e == cudaSuccess) rc = rd_split_plan(m, split_j, plan, pbytes, &info, s);
-    if (rc == RD_OK && e == cudaSuccess) e = cudaMalloc(&X, (size_t)info.x_rows * (size_t)ld * 2);
+    if (lowmem) info.chunk_cols = 8192;
+    const int64_t ldx = lowmem ? info.chunk_cols : ld;
+    if (rc == RD_OK && e == cudaSuccess) e = cudaMalloc(&X, (size_t)info.x_rows * (size_t)ldx * 2);
     if (e != cudaSuccess) {
       set_cuda_error(e);
       rc = (e == cudaErrorMemoryAllocation) ? RD_ERR_NOMEM : RD_ERR_CUDA;
     }
     if (rc == RD_OK)
-      rc = rd_power_until_periodic_split(A, ld, &info, plan, X, ld, kGammaKmax, work, wbytes, g.data(), &k, &p, &q, s);
+      rc = rd_power_until_periodic_split(A, ld, &info, plan, X, ldx, kGammaKmax, work, wbytes, g.data(), &k, &p, &q, s);
     if (s) cudaStreamSynchronize(s);
     if (plan) cudaFree(plan);
     if (X) cudaFree(X);
-    if (A) cudaFree(A);
+    if (A_own) cudaFree(A_own);
     if (work) cudaFree(work);
     if (s) cudaStreamDestroy(s);
     return finish_cached(rc, g, k, p, q, out);
@@ -534,7 +551,7 @@ rd_status compute_cached(int m, Cached* out) {
   if (s) cudaStreamSynchronize(s);
   if (start) cudaFree(start);
   if (rec) cudaFree(rec);
-  if (A) cudaFree(A);
+  if (A_own) cudaFree(A_own);
   if (work) cudaFree(work);
   if (s) cudaStreamDestroy(s);
   return finish_cached(rc, g, k, p, q, out);

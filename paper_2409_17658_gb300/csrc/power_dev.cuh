@@ -88,6 +88,7 @@ __device__ __forceinline__ void init_state_body(PowerState* st, int kmax, int sl
     for (int l = 0; l < 4; ++l) st->lvl_done[l] = 0;
     st->queue = 0;
     st->exited = 0;
+    st->far_i = kFarNone;
   }
   int64_t* off = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(st) + kStateHeader);
   int64_t* gam = off + (kmax + 1);
@@ -204,7 +205,7 @@ __device__ __forceinline__ void finalize_body(PowerState* st) {
   for (int i = 1 + (int)threadIdx.x; i < kn; i += 32) {
     if (hs[i] != hk) continue;
     if (kn - i >= st->slots) {
-      atomicOr(&st->err, kErrRing);  // the matching power has left the ring: cannot verify
+      atomicMin(&st->far_i, i);  // the matching power has left the ring: decided after the compare
       continue;
     }
     const int slot = atomicAdd(&st->ncand, 1);
@@ -256,14 +257,23 @@ __device__ __forceinline__ void compare_resolve_body(PowerState* st, int16_t* ri
     if (!(*(volatile int32_t*)&st->mismatch[c]) && (found < 0 || i < found)) found = i;
   }
   volatile int64_t* off = st_offset(st);
+  const int32_t far = *(volatile int32_t*)&st->far_i;
   if (found >= 1) {
     st->found_i = found;
     st->found_j = kn;
     st->found_q = off[kn] - off[found];
     st->done = 1;
+  } else if (far != kFarNone) {
+    // no power in the ring equals P_kn, but one that has left it has the same hash: stop, and leave
+    // the pair for a caller that can re-derive P_far
+    st->found_i = far;
+    st->found_j = kn;
+    st->err |= kErrRing;
+    st->done = 3;
   } else if (kn >= st->kmax) {
     st->done = 2;
   }
+  st->far_i = kFarNone;
   st->k = kn;
   st->mu = kInf;
   st->dmin = kInf;

@@ -37,7 +37,12 @@ struct PowerState {
   uint32_t lvl_done[4];
   uint32_t queue;
   uint32_t exited;
+  // the smallest earlier power whose hash matches the new one but which has left the ring (kFarNone: none);
+  // when no power in the ring matches exactly, the search stops with kErrRing and found_i = far_i,
+  // found_j = the new power, so a caller that can re-derive that power may still verify the relation
+  int32_t far_i;
 };
+constexpr int32_t kFarNone = 0x7FFFFFFF;
 
 constexpr size_t kStateHeader = 256;
 static_assert(sizeof(PowerState) <= kStateHeader, "state header too large");

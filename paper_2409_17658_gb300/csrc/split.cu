@@ -1348,6 +1348,93 @@ extern "C" rd_status rd_split_minplus(const rd_split_info_t* info, const void* p
   return RD_OK;
 }
 
+namespace rd {
+namespace {
+
+// Plain passes over an N x N power (row-major, leading dimension ld), blocks striding over rows and threads
+// over 16-byte chunks; entries past column N are padding and ignored.
+__global__ void plain_min_kernel(const int16_t* __restrict__ X, int64_t N, int64_t ld, int32_t* out) {
+  int32_t m = kInf;
+  for (int64_t i = blockIdx.x; i < N; i += gridDim.x)
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) m = min(m, (int32_t)X[i * ld + j]);
+  for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+  if ((threadIdx.x & 31) == 0 && m < kInf) atomicMin(out, m);
+}
+
+// dst = src - mu on finite entries (the search's normalisation of a power)
+__global__ void plain_normalise_kernel(const int16_t* __restrict__ src, int16_t* __restrict__ dst, int64_t N,
+                                       int64_t ld, const int32_t* mu_dev) {
+  const int32_t mu_raw = *mu_dev;
+  const int32_t mu = (mu_raw >= kInf) ? 0 : mu_raw;
+  for (int64_t i = blockIdx.x; i < N; i += gridDim.x)
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+      const int32_t x = src[i * ld + j];
+      dst[i * ld + j] = (int16_t)(x == kInf ? kInf : x - mu);
+    }
+}
+
+// *flag = 1 when a and b differ in some entry of the N x N matrix
+__global__ void plain_differ_kernel(const int16_t* __restrict__ a, const int16_t* __restrict__ b, int64_t N,
+                                    int64_t ld, int32_t* flag) {
+  int d = 0;
+  for (int64_t i = blockIdx.x; i < N && !d; i += gridDim.x)
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) d |= (a[i * ld + j] != b[i * ld + j]);
+  if (__syncthreads_or(d) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+// The search stopped at P_j with P_i (i < j) its only hash match, out of the ring.  Re-derive P_i from A(G)
+// in the two ring slots that do not hold P_j -- A(G) rebuilt, normalised, then i - 1 row-split products each
+// normalised, the same arithmetic as the search -- and compare it with P_j entry by entry.  The search state's
+// scalar fields serve as device scratch (the search has stopped).
+rd_status verify_far_pair(const rd_split_info_t& info, const void* plan, int16_t* X, int64_t ldx, int64_t lda,
+                          void* work_dev, int kmax, int slots, int i, int j, bool* equal, cudaStream_t s) {
+  const int64_t N = info.N;
+  PowerState* st = reinterpret_cast<PowerState*>(work_dev);
+  int16_t* ring = reinterpret_cast<int16_t*>(static_cast<char*>(work_dev) + state_bytes(kmax));
+  const int64_t se = (int64_t)(slot_bytes(N, lda) / 2);
+  int16_t* pj = ring + (int64_t)(j % slots) * se;
+  int16_t* cur = ring + (int64_t)((j + 1) % slots) * se;
+  int16_t* nxt = ring + (int64_t)((j + 2) % slots) * se;
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned grid = (unsigned)(sms * 8);
+  rd_status rc = rd_build_transfer(info.m, cur, lda, s);
+  if (rc != RD_OK) return rc;
+  cudaError_t e = launch_fill_i32(&st->mu, kInf, s);
+  if (e == cudaSuccess) {
+    plain_min_kernel<<<grid, 256, 0, s>>>(cur, N, lda, &st->mu);
+    plain_normalise_kernel<<<grid, 256, 0, s>>>(cur, nxt, N, lda, &st->mu);  // P_1
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return fail(e);
+  int16_t* p = nxt;
+  int16_t* q = cur;
+  for (int t = 1; t < i; ++t) {  // P_(t+1) from P_t
+    rc = rd_split_minplus(&info, plan, p, lda, X, ldx, q, lda, &st->mu, s);
+    if (rc != RD_OK) return rc;
+    plain_normalise_kernel<<<grid, 256, 0, s>>>(q, q, N, lda, &st->mu);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(e);
+    int16_t* t2 = p;
+    p = q;
+    q = t2;
+  }
+  e = launch_fill_i32(&st->dmin, 0, s);
+  if (e == cudaSuccess) {
+    plain_differ_kernel<<<grid, 256, 0, s>>>(p, pj, N, lda, &st->dmin);
+    e = cudaGetLastError();
+  }
+  int32_t differ = 1;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&differ, &st->dmin, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(e);
+  *equal = differ == 0;
+  return RD_OK;
+}
+
+}  // namespace
+}  // namespace rd
+
 extern "C" rd_status rd_power_until_periodic_split(const int16_t* A_dev, int64_t lda, const rd_split_info_t* info,
                                                    const void* plan_dev, int16_t* X_dev, int64_t ldx, int kmax,
                                                    void* work_dev, size_t work_bytes, int64_t* gamma_host,
@@ -1366,6 +1453,27 @@ extern "C" rd_status rd_power_until_periodic_split(const int16_t* A_dev, int64_t
   c.p2.in = X_dev;
   c.p2.ldin = ldx;
   c.info = *info;
-  return power_search(A_dev, N, lda, kmax, work_dev, work_bytes, split_power_product, &c, gamma_host, k_out, p_out,
-                      q_out, s, split_normalises(*info));
+  rd_status rc = power_search(A_dev, N, lda, kmax, work_dev, work_bytes, split_power_product, &c, gamma_host, k_out,
+                              p_out, q_out, s, split_normalises(*info));
+  if (rc != RD_ERR_NOMEM) return rc;
+  // Stopped with a hash match out of the ring?  Then verify it by re-deriving the earlier power.
+  PowerState h{};
+  cudaError_t e = cudaMemcpyAsync(&h, work_dev, sizeof(PowerState), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(e);
+  if (!(h.done == 3 && h.err == kErrRing && h.slots >= 3 && h.found_i >= 1 && h.found_j > h.found_i)) return rc;
+  bool equal = false;
+  rc = verify_far_pair(*info, plan_dev, X_dev, ldx, lda, work_dev, kmax, h.slots, h.found_i, h.found_j, &equal, s);
+  if (rc != RD_OK) return rc;
+  if (!equal) return RD_ERR_NOMEM;  // a hash collision with a power that has left the ring
+  int64_t off_i = 0, off_j = 0;
+  const int64_t* off = reinterpret_cast<const int64_t*>(static_cast<const char*>(work_dev) + kStateHeader);
+  e = cudaMemcpyAsync(&off_i, off + h.found_i, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&off_j, off + h.found_j, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(e);
+  *k_out = h.found_i;
+  *p_out = h.found_j - h.found_i;
+  *q_out = off_j - off_i;
+  return RD_OK;
 }

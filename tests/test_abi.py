@@ -85,8 +85,10 @@ def test_work_layout(rd):
     assert slot >= n * ld * 2 and slot % 256 == 0 and b5 - b2 == 3 * slot
     offs = [rd.power_slot(n, ld, kmax, b5, k) for k in range(1, 11)]
     assert len(set(offs[:5])) == 5 and offs[5] == offs[0]  # P_k lives in slot k mod 5
+    # power 0's slot (where a caller short of memory may build A) is the one P_5 later fills
+    assert rd.power_slot(n, ld, kmax, b5, 0) == offs[4]
     with pytest.raises(rd.RdError):
-        rd.power_slot(n, ld, kmax, b5, 0)
+        rd.power_slot(n, ld, kmax, b5, -1)
 
 
 def test_split_plan_sizes(rd):

@@ -317,6 +317,26 @@ def test_power_multi_mixes_split_and_sparse_runs(rd, torch_mod, orc, graph_steps
     assert [int(x) for x in res[8]["gamma"][1:res[8]["j"] + 1]] == o9["gamma"][1:o9["j"] + 1]
 
 
+@pytest.mark.parametrize("m", [7, 9])
+def test_power_split_short_ring_rederives(rd, torch_mod, orc, m):
+    """A ring of 3 slots is shorter than the period (5): when P_(k+p)'s hash matches P_k, P_k has left the ring,
+    so the search stops, re-derives P_k from A(G) in the two spare slots and compares it with P_(k+p) entry by
+    entry.  The relation and gamma equal the oracle's (m = 9: its row-streamed search)."""
+    kmax = 40
+    A, n = rd.transfer_matrix(m)
+    plan = rd.split_plan(m, x_ld=A.stride(0))
+    work = rd.power_workspace(n, A.stride(0), kmax, 3)
+    r = rd.power_until_periodic_split(A, plan, kmax, work)
+    if m == 7:
+        o = orc.power_until_periodic(m, kmax=kmax)
+        want_gamma = [int(x) for x in o["gamma"][1:o["j"] + 1]]
+    else:
+        o = oracle_m9()
+        want_gamma = o["gamma"][1:o["j"] + 1]
+    assert r["found"] and (r["k"], r["p"], r["q"]) == (o["k"], o["p"], o["q"])
+    assert [int(x) for x in r["gamma"][1:r["j"] + 1]] == want_gamma
+
+
 @pytest.mark.parametrize("j", [1, 2, 5, 6])
 def test_power_split_every_split_point_m7(rd, torch_mod, orc, j):
     """The period search through unbalanced splits (fibers of up to 1085 slots, metadata read from global
