@@ -373,7 +373,8 @@ typedef struct {
   int32_t chunk_cols;
 } rd_split_info_t;
 
-/* rd_split_default_j -- the split used by default, floor(m / 2); 0 when m is
+/* rd_split_default_j -- the split used by default: floor(m / 2) for m <= 10,
+ * ceil(m / 2) from m = 11 on (smaller largest fibers there); 0 when m is
  * outside [2, RD_MAX_M] or a part would exceed 8 rows. */
 int rd_split_default_j(int m);
 

@@ -1146,7 +1146,11 @@ using namespace rd;
 
 extern "C" int rd_split_default_j(int m) {
   if (m < 2 || m > RD_MAX_M) return 0;
-  const int j = m / 2;
+  // The lower half gets the extra row up to m = 10 and the upper half from m = 11 on: at m = 11 the split
+  // after row 5 gives pass-2 fibers of up to 1085 slots (32-column slabs), after row 6 fibers of at most
+  // 848, and the product takes 137 ms against 161 ms (tuned 135 against 153); for m = 5, 7, 9 the two
+  // choices are within 2 % of each other.
+  const int j = (m >= 11) ? m - m / 2 : m / 2;
   return (j <= kSplitMaxLen && m - j <= kSplitMaxLen) ? j : 0;
 }
 

@@ -92,7 +92,7 @@ def test_work_layout(rd):
 
 
 def test_split_plan_sizes(rd):
-    assert [rd.split_default_j(m) for m in (1, 2, 3, 9, 10, 15, 16)] == [0, 1, 1, 4, 5, 7, 0]
+    assert [rd.split_default_j(m) for m in (1, 2, 3, 9, 10, 11, 15, 16)] == [0, 1, 1, 4, 5, 6, 8, 0]
     b = {j: rd.split_plan_bytes(10, j) for j in range(2, 9)}
     # the plan is small next to one 64769 x 64776 int16 matrix (8.4 GB), smallest for the balanced split
     assert all(0 < v < 256 << 20 for v in b.values())
