@@ -1355,35 +1355,64 @@ extern "C" rd_status rd_split_minplus(const rd_split_info_t* info, const void* p
 namespace rd {
 namespace {
 
-// Plain passes over an N x N power (row-major, leading dimension ld), blocks striding over rows and threads
-// over 16-byte chunks; entries past column N are padding and ignored.
+// Plain passes over an N x N power (row-major, leading dimension ld a multiple of 8, 16-byte aligned rows),
+// blocks striding over rows and threads over 16-byte chunks; entries past column N are padding and ignored.
+__device__ __forceinline__ uint32_t tail_keep(int64_t j0, int64_t N, int q) {
+  // halfword mask of word q of the chunk at column j0: 0xFFFF for columns < N
+  const int64_t c = j0 + 2 * q;
+  return (c < N ? 0x0000FFFFu : 0u) | (c + 1 < N ? 0xFFFF0000u : 0u);
+}
+
 __global__ void plain_min_kernel(const int16_t* __restrict__ X, int64_t N, int64_t ld, int32_t* out) {
-  int32_t m = kInf;
+  uint32_t m2 = kInf2;
+  const int64_t cpr = (N + 7) / 8;
   for (int64_t i = blockIdx.x; i < N; i += gridDim.x)
-    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) m = min(m, (int32_t)X[i * ld + j]);
+    for (int64_t c = threadIdx.x; c < cpr; c += blockDim.x) {
+      const uint4 v = __ldcg(reinterpret_cast<const uint4*>(X + i * ld + c * 8));
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t keep = tail_keep(c * 8, N, q);
+        m2 = __vminu2(m2, (w[q] & keep) | (kInf2 & ~keep));
+      }
+    }
+  int32_t m = (int32_t)min(m2 & 0xFFFFu, m2 >> 16);
   for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
   if ((threadIdx.x & 31) == 0 && m < kInf) atomicMin(out, m);
 }
 
-// dst = src - mu on finite entries (the search's normalisation of a power)
+// dst = src - mu on finite entries (the search's normalisation of a power); padding columns copied as they are
 __global__ void plain_normalise_kernel(const int16_t* __restrict__ src, int16_t* __restrict__ dst, int64_t N,
                                        int64_t ld, const int32_t* mu_dev) {
   const int32_t mu_raw = *mu_dev;
-  const int32_t mu = (mu_raw >= kInf) ? 0 : mu_raw;
+  const uint32_t mu2 = (uint32_t)((mu_raw >= kInf) ? 0 : mu_raw) * 0x00010001u;
+  const int64_t cpr = (N + 7) / 8;
   for (int64_t i = blockIdx.x; i < N; i += gridDim.x)
-    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
-      const int32_t x = src[i * ld + j];
-      dst[i * ld + j] = (int16_t)(x == kInf ? kInf : x - mu);
+    for (int64_t c = threadIdx.x; c < cpr; c += blockDim.x) {
+      const uint4 v = __ldcg(reinterpret_cast<const uint4*>(src + i * ld + c * 8));
+      uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t isinf = __vcmpeq2(w[q], kInf2);
+        w[q] = __vsub2(w[q], mu2 & ~isinf);
+      }
+      *reinterpret_cast<uint4*>(dst + i * ld + c * 8) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
 // *flag = 1 when a and b differ in some entry of the N x N matrix
 __global__ void plain_differ_kernel(const int16_t* __restrict__ a, const int16_t* __restrict__ b, int64_t N,
                                     int64_t ld, int32_t* flag) {
-  int d = 0;
-  for (int64_t i = blockIdx.x; i < N && !d; i += gridDim.x)
-    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) d |= (a[i * ld + j] != b[i * ld + j]);
-  if (__syncthreads_or(d) && threadIdx.x == 0) atomicOr(flag, 1);
+  uint32_t d = 0;
+  const int64_t cpr = (N + 7) / 8;
+  for (int64_t i = blockIdx.x; i < N; i += gridDim.x)
+    for (int64_t c = threadIdx.x; c < cpr; c += blockDim.x) {
+      const uint4 x = __ldcg(reinterpret_cast<const uint4*>(a + i * ld + c * 8));
+      const uint4 y = __ldcg(reinterpret_cast<const uint4*>(b + i * ld + c * 8));
+      d |= ((x.x ^ y.x) & tail_keep(c * 8, N, 0)) | ((x.y ^ y.y) & tail_keep(c * 8, N, 1)) |
+           ((x.z ^ y.z) & tail_keep(c * 8, N, 2)) | ((x.w ^ y.w) & tail_keep(c * 8, N, 3));
+    }
+  if (__syncthreads_or(d != 0) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
 // The search stopped at P_j with P_i (i < j) its only hash match, out of the ring.  Re-derive P_i from A(G)
