@@ -344,7 +344,7 @@ rd_status rd_sparse_tune(const int16_t *A, int64_t lda, int64_t N, void *scratch
  *            some word (rho, sigma) has rho admitted by pi (the others are
  *            RD_INF and not stored);
  *   plan_bytes  device bytes of the plan;
- *   w1, w2   column-slab widths of the two passes (32, 64 or 128); chosen
+ *   w1, w2   column-slab widths of the two passes (32, 64, 128 or 256); chosen
  *            by rd_split_plan, and a caller may set another of these values
  *            if its staged fiber fits in shared memory (else RD_ERR_ARG);
  *   slots1, slots2  rows staged per fiber at most (words of one sigma in
@@ -578,7 +578,7 @@ rd_status rd_power_until_periodic_noalloc(const int16_t *A_dev, int64_t N, int64
  *                        rd_tune_bucket(K); p[0] = S in {1, 2, 4, 8},
  *                        p[1] = output tile 0 (128 x 256) or 1 (128 x 128);
  *   RD_TUNE_SPLIT        key = m, aux = j; p[0..3] = w1, k1, w2, k2 (widths
- *                        32, 64 or 128; slabs per CTA 1..64);
+ *                        32, 64, 128 or 256; slabs per CTA 1..64);
  *   RD_TUNE_SPARSE_R     key = rd_tune_bucket(N), aux = 0; p[0] = R in
  *                        {1, 2, 4, 8};
  * ms is the time the autotuner measured for the entry (informational).
@@ -634,7 +634,7 @@ rd_status rd_tune_gemm(const int16_t *A, int64_t lda, const int16_t *B, int64_t 
 /*
  * rd_tune_split -- autotuner for the launch shape of the row-split passes of
  * a built plan (arguments as in rd_split_minplus; X and C are overwritten):
- * times rd_split_minplus over the widths {32, 64, 128} that fit and slabs per
+ * times rd_split_minplus over the widths {32, 64, 128, 256} that fit and slabs per
  * CTA {1, 2, 4, 8, 16, 32}, first for pass 1 with pass 2 as in *info, then
  * for pass 2 with pass 1 at its best (one warm-up and reps >= 1 timed
  * products per candidate).  Writes the best w1, k1, w2, k2 into *info,

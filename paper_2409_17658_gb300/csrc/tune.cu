@@ -37,8 +37,8 @@ bool entry_ok(const rd_tune_entry_t& t) {
              (t.p[1] == 0 || t.p[1] == 1);
     case RD_TUNE_SPLIT:
       return t.key >= 2 && t.key <= RD_MAX_M && t.aux >= 1 && t.aux < t.key &&
-             (t.p[0] == 32 || t.p[0] == 64 || t.p[0] == 128) && t.p[1] >= 1 && t.p[1] <= 64 &&
-             (t.p[2] == 32 || t.p[2] == 64 || t.p[2] == 128) && t.p[3] >= 1 && t.p[3] <= 64;
+             (t.p[0] == 32 || t.p[0] == 64 || t.p[0] == 128 || t.p[0] == 256) && t.p[1] >= 1 && t.p[1] <= 64 &&
+             (t.p[2] == 32 || t.p[2] == 64 || t.p[2] == 128 || t.p[2] == 256) && t.p[3] >= 1 && t.p[3] <= 64;
     case RD_TUNE_SPARSE_R:
       return t.key >= 0 && t.key <= 63 && t.aux == 0 && is_pow2_le8(t.p[0]);
     default:
@@ -223,7 +223,7 @@ extern "C" rd_status rd_tune_split(rd_split_info_t* info, const void* plan_dev, 
   rd_status rc = RD_OK;
   float best_ms = time_calls(product, reps, ev.e0, ev.e1, s, &rc);
   if (rc != RD_OK) return rc;
-  const int ws[3] = {32, 64, 128}, ks[6] = {1, 2, 4, 8, 16, 32};
+  const int ws[4] = {32, 64, 128, 256}, ks[6] = {1, 2, 4, 8, 16, 32};
   for (int pass = 1; pass <= 2; ++pass) {
     const int slots = pass == 1 ? info->slots1 : info->slots2;
     for (int w : ws) {

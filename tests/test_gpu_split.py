@@ -111,8 +111,8 @@ def test_split_minplus_all_infinite_and_slab_widths(rd, torch_mod, orc):
     b = inputs.matrix(n, n, seed=80, dist="u32")
     B = upload(torch, b, junk=I16_INF)
     want = orc.minplus_i16(to_i16(orc.transfer(m)), b)
-    for w1 in (32, 64, 128):
-        for w2 in (32, 64, 128):
+    for w1 in (32, 64, 128, 256):
+        for w2 in (32, 64, 128, 256):
             plan["info"].w1, plan["info"].w2 = w1, w2
             C.fill_(0)
             rd.split_minplus(plan, B, C)

@@ -167,7 +167,7 @@ def test_tune_split_m7_then_plans_and_searches_use_it(rd, orc):
     assert np.array_equal(r["gamma"][1:r["j"] + 1], o["gamma"][1:o["j"] + 1])
 
 
-@pytest.mark.parametrize("shape", [(32, 1), (64, 64), (128, 2), (32, 32)])
+@pytest.mark.parametrize("shape", [(32, 1), (64, 64), (128, 2), (32, 32), (256, 1), (256, 16)])
 def test_split_shapes_from_the_table_are_bit_exact(rd, orc, shape):
     """Every width and slabs-per-CTA the tuner may pick, installed through the table, at m = 6."""
     import torch

@@ -49,7 +49,7 @@ def test_set_get_lookup_round_trip(rd):
     dict(mode="gemm_splitk", key=10, aux=10, p=[2, 2]),        # tile 0 or 1
     dict(mode="split", key=9, aux=9, p=[64, 8, 64, 8]),      # j must be < m
     dict(mode="split", key=1, aux=0, p=[64, 8, 64, 8]),      # m >= 2
-    dict(mode="split", key=9, aux=4, p=[96, 8, 64, 8]),      # width not 32, 64 or 128
+    dict(mode="split", key=9, aux=4, p=[96, 8, 64, 8]),      # width not 32, 64, 128 or 256
     dict(mode="split", key=9, aux=4, p=[64, 0, 64, 8]),      # slabs per CTA in 1..64
     dict(mode="split", key=9, aux=4, p=[64, 8, 64, 65]),
     dict(mode="sparse_r", key=15, aux=1, p=[2]),             # aux must be 0
