@@ -441,6 +441,22 @@ def gemm_sweep(rd, torch, sizes=(1024, 2048, 4096, 32768)) -> dict:
         gops = float(n) ** 3 / (ms * 1e-3) / 1e9
         out[f"N={n}"] = {"ms": ms, "gops": gops, "frac_of_peak": gops / PEAK_GOPS, "split_k": tuned["p"][0],
                          "tile": "128x128" if tuned["p"][1] else "128x256", "tuner_ms": tuned["ms"]}
+        if n <= 4096:
+            # the stream-K form: the resident CTAs share the (tile, k-tile) units evenly
+            work = rd.minplus_gemm_streamk_workspace(n, n, n)
+            C2 = torch.empty_like(C)
+            rd.minplus_gemm_streamk(A, B, C2, work)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                rd.minplus_gemm_streamk(A, B, C2, work)
+            e1.record()
+            torch.cuda.synchronize()
+            ms_sk = e0.elapsed_time(e1) / reps
+            gops_sk = float(n) ** 3 / (ms_sk * 1e-3) / 1e9
+            out[f"N={n}"]["streamk"] = {"ms": ms_sk, "gops": gops_sk, "frac_of_peak": gops_sk / PEAK_GOPS,
+                                        "same_result": bool(torch.equal(C, C2))}
+            del work, C2
         del A, B, C
         torch.cuda.empty_cache()
     return out

@@ -122,6 +122,32 @@ rd_status rd_minplus_gemm(const int16_t *A, int64_t lda, const int16_t *B, int64
                           int64_t M, int64_t N, int64_t K, int32_t *min_out, cudaStream_t s);
 
 /*
+ * rd_minplus_gemm_streamk -- the same product C = A (x) B as rd_minplus_gemm
+ * (Sec. 3), for products with few 128 x 256 output tiles.  The work is cut
+ * into (output tile, 32-deep k-tile) units, and exactly the resident CTAs (two
+ * per SM) take equal contiguous runs of them, so every SM has the same share
+ * whatever the tile count.  A CTA whose run starts or ends inside a tile leaves
+ * that partial tile in the workspace; the last CTA to finish the tile takes the
+ * minimum of the partials and writes C.  No CTA waits for another.  The result
+ * is bit-identical to rd_minplus_gemm.
+ * work_dev: caller-owned device memory, 256-byte aligned, at least
+ * rd_minplus_gemm_streamk_work_bytes(M, N, K) bytes (about 40 MB on a 152-SM
+ * GPU: partial tiles, then one counter per output tile).  It must be
+ * zero-filled before its first use; every call leaves its counters at zero, so
+ * the same workspace serves later calls of any shape whose size it covers.  One
+ * call at a time per workspace: calls on different streams need separate
+ * workspaces.  The size depends on the current device's SM count.
+ * M = 1, N = 0 or K = 0, and products too large for 32-bit unit numbers
+ * (units x grid >= 2^32, many waves of tiles), go to rd_minplus_gemm with the
+ * same result, and the workspace is then not touched.  Other conventions,
+ * min_out and errors as rd_minplus_gemm; RD_ERR_NOMEM for a short workspace.
+ */
+rd_status rd_minplus_gemm_streamk_work_bytes(int64_t M, int64_t N, int64_t K, size_t *bytes);
+rd_status rd_minplus_gemm_streamk(const int16_t *A, int64_t lda, const int16_t *B, int64_t ldb, int16_t *C,
+                                  int64_t ldc, int64_t M, int64_t N, int64_t K, void *work_dev, size_t work_bytes,
+                                  int32_t *min_out, cudaStream_t s);
+
+/*
  * rd_minplus_gemm_host -- rd_minplus_gemm (Sec. 3's product) for operands in
  * host memory: A (M x K, row stride lda elements) and B (K x N, ldb) are read
  * from host memory and C (M x N, ldc) is written to host memory.  Host strides

@@ -112,6 +112,10 @@ def _lib():
         lib.rd_measure_addmin_peak.argtypes = [vp, sz, i64, vp, vp]
         lib.rd_gamma_R_clear.argtypes = []
         lib.rd_gamma_R_clear.restype = st
+        lib.rd_minplus_gemm_streamk_work_bytes.argtypes = [i64, i64, i64, vp]
+        lib.rd_minplus_gemm_streamk_work_bytes.restype = st
+        lib.rd_minplus_gemm_streamk.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, vp, sz, vp, vp]
+        lib.rd_minplus_gemm_streamk.restype = st
         lib.rd_minplus_gemm_host_work_bytes.argtypes = [i64, i64, i64, vp]
         lib.rd_minplus_gemm_host_work_bytes.restype = st
         lib.rd_minplus_gemm_host.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, vp, sz, vp, vp]
@@ -196,6 +200,35 @@ def minplus_gemm(A, B, C, M: int | None = None, N: int | None = None, K: int | N
     mo = _dptr(min_out) if min_out is not None else None
     _check(_lib().rd_minplus_gemm(_dptr(A), A.stride(0), _dptr(B), B.stride(0), _dptr(C), C.stride(0), M, N, K,
                                   mo, _stream(stream)), "rd_minplus_gemm")
+
+
+def minplus_gemm_streamk_work_bytes(M: int, N: int, K: int) -> int:
+    out = ctypes.c_size_t()
+    _check(_lib().rd_minplus_gemm_streamk_work_bytes(M, N, K, ctypes.byref(out)),
+           "rd_minplus_gemm_streamk_work_bytes")
+    return out.value
+
+
+def minplus_gemm_streamk_workspace(M: int, N: int, K: int, device="cuda"):
+    """A zero-filled workspace for rd_minplus_gemm_streamk (each call leaves it zero-filled again)."""
+    import torch
+
+    return torch.zeros(minplus_gemm_streamk_work_bytes(M, N, K), dtype=torch.uint8, device=device)
+
+
+def minplus_gemm_streamk(A, B, C, work, M: int | None = None, N: int | None = None, K: int | None = None,
+                         min_out=None, stream=None) -> None:
+    """rd_minplus_gemm_streamk: C[:M, :N] = A[:M, :K] (x) B[:K, :N], the k-tiles shared evenly by the resident
+    CTAs; `work` from minplus_gemm_streamk_workspace."""
+    for t in (A, B, C):
+        assert t.dim() == 2 and t.stride(1) == 1
+    M = C.shape[0] if M is None else M
+    N = C.shape[1] if N is None else N
+    K = A.shape[1] if K is None else K
+    mo = _dptr(min_out) if min_out is not None else None
+    _check(_lib().rd_minplus_gemm_streamk(_dptr(A), A.stride(0), _dptr(B), B.stride(0), _dptr(C), C.stride(0), M, N,
+                                          K, _dptr(work), work.numel() * work.element_size(), mo, _stream(stream)),
+           "rd_minplus_gemm_streamk")
 
 
 def minplus_gemv(x, B, y, N: int | None = None, K: int | None = None, min_out=None, stream=None) -> None:

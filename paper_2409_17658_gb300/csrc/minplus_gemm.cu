@@ -370,6 +370,150 @@ __global__ void __launch_bounds__(NT, BNT == BN ? 2 : 3) minplus_gemm_splitk_ker
   cluster.sync();  // no CTA leaves while others may still read its shared memory
 }
 
+// ---- stream-K for products with few output tiles.  The units of work are (output tile, k-tile) pairs,
+// tile by tile in the grouped order; a grid of exactly the resident CTAs (two per SM) takes equal
+// contiguous runs of them, so every SM does the same number of add-mins whatever the tile count.  A run
+// covers whole tiles in its middle and may start and end partway through a tile.  A CTA computes each
+// segment of its run into a partial tile in shared memory; a whole tile goes straight to C.  A partial
+// tile goes to the CTA's slot of the workspace (slot 0 for the tile of its first unit, slot 1 for the
+// tile of its last), then the CTA counts itself in on that tile; the CTA that arrives last takes the
+// minimum of its own partial and the others' slots and writes C.  Min is exact and order-free, so the
+// result is bit-identical to one CTA per tile.  Nothing waits on another CTA; the last CTA resets the
+// tile's counter, so the workspace's counters are zero again when the launch ends.
+// Unit arithmetic is 32-bit: the host takes this form only when U * gridDim.x < 2^32.
+struct StreamK {
+  uint32_t gx, gy;  // column and row tiles of C
+  uint32_t KT;      // k-tiles per tile
+  uint32_t U;       // units: gx * gy * KT
+  uint4* part;      // [2 * gridDim.x][BM * BN / 8] partial tiles
+  uint32_t* cnt;    // [gx * gy] CTAs arrived per tile; zero between launches
+};
+
+constexpr int kSkVec = BM * BN / 8;  // 16-byte vectors of one partial tile
+constexpr int kSkBatch = 8;          // vectors a thread reduces at once (kSkVec is a multiple of NT * kSkBatch)
+static_assert(kSkVec % (NT * kSkBatch) == 0, "the reduction's batches cover the tile exactly");
+static_assert((size_t)kSkVec * 16 <= SMEM_BYTES, "a partial tile fits in the staging buffers");
+
+__device__ __forceinline__ uint32_t sk_first_unit(uint32_t c, uint32_t U, uint32_t G) { return c * U / G; }
+// the CTA whose run holds unit u: the largest c with sk_first_unit(c) <= u
+__device__ __forceinline__ uint32_t sk_cta_of(uint32_t u, uint32_t U, uint32_t G) { return ((u + 1) * G - 1) / U; }
+
+// Writes vector v of a 128 x 256 tile at (m0, n0) of C (the layout gemm_tile<true> leaves in shared
+// memory: row v / 32, columns (v % 32 / 16) * 128 + (v % 16) * 8 ..), folding its entries into vmin/emin.
+__device__ __forceinline__ void sk_store(const GemmParams& p, int64_t m0, int64_t n0, int v, const uint4& r,
+                                         uint32_t& vmin, int32_t& emin) {
+  const int row = v / (BN / 8), c8 = v % (BN / 8);
+  const int64_t gi = m0 + row, gj = n0 + (c8 / 16) * 128 + (c8 % 16) * 8;
+  if (gi >= p.M || gj >= p.N) return;
+  if (gj + 8 <= p.N) {
+    *reinterpret_cast<uint4*>(p.C + gi * p.ldc + gj) = r;
+    vmin = __vmins2(__vmins2(vmin, r.x), __vmins2(__vmins2(r.y, r.z), r.w));
+  } else {
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      if (gj + e < p.N) {
+        const int32_t x = (int32_t)((w[e >> 1] >> (16 * (e & 1))) & 0xFFFF);
+        p.C[gi * p.ldc + gj + e] = (int16_t)x;
+        emin = min(emin, x);
+      }
+  }
+}
+
+// The segment a CTA works on: its first unit and the tile's coordinates, derived from the CTA's run.
+struct SkSeg {
+  uint32_t t, ka, kb;
+  int64_t m0, n0;
+};
+__device__ __forceinline__ SkSeg sk_segment(const StreamK& sk, uint32_t u, uint32_t u_end) {
+  SkSeg g;
+  g.t = u / sk.KT;
+  g.ka = u - g.t * sk.KT;
+  g.kb = (sk.KT - g.ka < u_end - u) ? sk.KT : g.ka + (u_end - u);
+  // the grouped order of grouped_tile, in 32-bit arithmetic
+  const uint32_t per_group = (uint32_t)kGroupM * sk.gx, first_m = g.t / per_group * kGroupM;
+  const uint32_t group_rows = (sk.gy - first_m < (uint32_t)kGroupM) ? sk.gy - first_m : (uint32_t)kGroupM;
+  const uint32_t in_group = g.t % per_group;
+  g.m0 = (int64_t)(first_m + in_group % group_rows) * BM;
+  g.n0 = (int64_t)(in_group / group_rows) * BN;
+  return g;
+}
+
+// Folds a thread's minimum of the entries it wrote into min_out (one atomic per warp).
+__device__ __forceinline__ void sk_min_out(int32_t* min_out, uint32_t vmin, int32_t emin) {
+  int32_t lm = min(emin, min((int32_t)(vmin & 0xFFFF), (int32_t)(vmin >> 16)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lm = min(lm, __shfl_xor_sync(0xFFFFFFFFu, lm, o));
+  if ((threadIdx.x & 31) == 0 && lm < kInf) atomicMin(min_out, lm);
+}
+
+__global__ void __launch_bounds__(NT, 2) minplus_gemm_streamk_kernel(GemmParams p, StreamK sk) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  // the run's position lives in shared memory, so no register is held across the tile's main loop
+  __shared__ uint32_t s_u;
+  __shared__ int s_last;
+  const uint4* T = reinterpret_cast<const uint4*>(smem);
+  if (threadIdx.x == 0) s_u = sk_first_unit(blockIdx.x, sk.U, gridDim.x);
+  __syncthreads();
+  for (;;) {
+    const uint32_t u = *(volatile uint32_t*)&s_u, u_end = sk_first_unit(blockIdx.x + 1, sk.U, gridDim.x);
+    if (u >= u_end) break;
+    {
+      const SkSeg g = sk_segment(sk, u, u_end);
+      const int64_t k0 = (int64_t)g.ka * BK, klen = (int64_t)(g.kb - g.ka) * BK;
+      const int64_t kext = (p.K - k0 < klen) ? p.K - k0 : klen;
+      gemm_tile<true, BN>(p.A + k0, p.B + k0 * p.ldb, nullptr, p.M, p.N, kext, p.lda, p.ldb, p.ldc, g.m0, g.n0,
+                          nullptr, nullptr, smem);
+    }
+    __syncthreads();  // the partial tile is complete in shared memory
+    const uint32_t G = gridDim.x, c = blockIdx.x;
+    const uint32_t uu = *(volatile uint32_t*)&s_u;
+    const SkSeg g = sk_segment(sk, uu, u_end);
+    uint32_t vmin = kInf2;
+    int32_t emin = kInf;
+    if (g.ka == 0 && g.kb == sk.KT) {
+      for (int v = threadIdx.x; v < kSkVec; v += NT) sk_store(p, g.m0, g.n0, v, T[v], vmin, emin);
+    } else {
+      const uint32_t cf = sk_cta_of(g.t * sk.KT, sk.U, G), cl = sk_cta_of((g.t + 1) * sk.KT - 1, sk.U, G);
+      const uint32_t first_tile = sk_first_unit(c, sk.U, G) / sk.KT;
+      uint4* mine = sk.part + (int64_t)(2 * c + (g.t == first_tile ? 0 : 1)) * kSkVec;
+      for (int v = threadIdx.x; v < kSkVec; v += NT) __stcg(mine + v, T[v]);
+      __threadfence();  // this CTA's partial is visible before it is counted
+      __syncthreads();
+      if (threadIdx.x == 0) s_last = (atomicAdd(sk.cnt + g.t, 1u) == cl - cf);
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        // kSkBatch vectors per thread at a time, each partial's kSkBatch loads in flight together
+        for (int v0 = threadIdx.x; v0 < kSkVec; v0 += NT * kSkBatch) {
+          uint4 r[kSkBatch];
+#pragma unroll
+          for (int i = 0; i < kSkBatch; ++i) r[i] = T[v0 + i * NT];
+          for (uint32_t q = cf; q <= cl; ++q) {
+            if (q == c) continue;
+            const uint32_t slot = 2 * q + (g.t == sk_first_unit(q, sk.U, G) / sk.KT ? 0 : 1);
+            const uint4* src = sk.part + (int64_t)slot * kSkVec + v0;
+            uint4 o[kSkBatch];
+#pragma unroll
+            for (int i = 0; i < kSkBatch; ++i) o[i] = __ldcg(src + i * NT);
+#pragma unroll
+            for (int i = 0; i < kSkBatch; ++i)
+              r[i] = make_uint4(__vmins2(r[i].x, o[i].x), __vmins2(r[i].y, o[i].y), __vmins2(r[i].z, o[i].z),
+                                __vmins2(r[i].w, o[i].w));
+          }
+#pragma unroll
+          for (int i = 0; i < kSkBatch; ++i) sk_store(p, g.m0, g.n0, v0 + i * NT, r[i], vmin, emin);
+        }
+        if (threadIdx.x == 0) sk.cnt[g.t] = 0u;  // every contributor has arrived: ready for the next launch
+      }
+    }
+    if (p.min_out != nullptr) sk_min_out(p.min_out, vmin, emin);
+    __syncthreads();  // the partial tile is read before the next segment's prologue overwrites it
+    if (threadIdx.x == 0) s_u = uu + (g.kb - g.ka);
+    __syncthreads();
+  }
+}
+
 // ---- batched products: one persistent launch over the tiles of up to kMaxBatch products
 
 constexpr int kMaxBatch = 128;
@@ -521,7 +665,7 @@ __global__ void __launch_bounds__(kGemvThreads) minplus_gemv_kernel(const int16_
   }
 }
 
-template <int WHICH>  // 0 plain, 1 ring, 2 batched, 3 split K, 4 plain narrow, 5 split K narrow
+template <int WHICH>  // 0 plain, 1 ring, 2 batched, 3 split K, 4 plain narrow, 5 split K narrow, 6 stream-K
 cudaError_t set_smem_attr() {
   static int done_dev[64] = {0};
   int dev = 0;
@@ -541,6 +685,9 @@ cudaError_t set_smem_attr() {
   else if (WHICH == 5)
     e = cudaFuncSetAttribute(minplus_gemm_splitk_kernel<BN_NARROW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes(BN_NARROW));
+  else if (WHICH == 6)
+    e = cudaFuncSetAttribute(minplus_gemm_streamk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES);
   else
     e = cudaFuncSetAttribute(minplus_gemm_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)SMEM_BYTES);
@@ -668,6 +815,85 @@ extern "C" rd_status rd_minplus_gemm(const int16_t* A, int64_t lda, const int16_
   p.A = A; p.lda = lda; p.B = B; p.ldb = ldb; p.C = C; p.ldc = ldc;
   p.M = M; p.N = N; p.K = K; p.min_out = min_out; p.diag_out = nullptr;
   e = launch_minplus_gemm(p, false, s);
+  if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
+  return RD_OK;
+}
+
+namespace rd {
+namespace {
+
+// Stream-K workspace: two partial tiles per CTA of the largest grid (two CTAs per SM), then the per-tile
+// counters.  The counters start at the same offset for every shape, so the zeros one call leaves are the
+// zeros the next call counts from, whatever its shape.
+struct SkLayout {
+  int64_t tiles, grid;
+  size_t cnt_bytes, part_bytes;
+};
+bool sk_layout(int64_t M, int64_t N, int64_t K, SkLayout* L) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                cudaSuccess || sms < 1)
+    return false;
+  const int64_t gx = (N + BN - 1) / BN, gy = (M + BM - 1) / BM, KT = (K + BK - 1) / BK;
+  L->tiles = gx * gy;
+  const int64_t U = L->tiles * KT;
+  L->grid = (U < 2 * (int64_t)sms) ? U : 2 * (int64_t)sms;
+  L->cnt_bytes = ((size_t)L->tiles * 4 + 255) / 256 * 256;
+  L->part_bytes = (size_t)(2 * sms) * 2 * (size_t)kSkVec * 16;
+  return true;
+}
+
+}  // namespace
+}  // namespace rd
+
+extern "C" rd_status rd_minplus_gemm_streamk_work_bytes(int64_t M, int64_t N, int64_t K, size_t* bytes) {
+  if (!bytes || M < 0 || N < 0 || K < 0) return RD_ERR_ARG;
+  SkLayout L;
+  if (!sk_layout(M, N, K, &L)) return RD_ERR_CUDA;
+  *bytes = L.cnt_bytes + L.part_bytes;
+  return RD_OK;
+}
+
+extern "C" rd_status rd_minplus_gemm_streamk(const int16_t* A, int64_t lda, const int16_t* B, int64_t ldb, int16_t* C,
+                                             int64_t ldc, int64_t M, int64_t N, int64_t K, void* work,
+                                             size_t work_bytes, int32_t* min_out, cudaStream_t s) {
+  if (M < 0 || N < 0 || K < 0) return RD_ERR_ARG;
+  if (M > 0 && N > 0) {
+    if (!C || !aligned16(C) || ldc < N || ldc % 8 != 0) return RD_ERR_ARG;
+    if (K > 0) {
+      if (!A || !B || !aligned16(A) || !aligned16(B)) return RD_ERR_ARG;
+      if (lda < K || lda % 8 != 0 || ldb < N || ldb % 8 != 0) return RD_ERR_ARG;
+    }
+  }
+  if (M <= 1 || N == 0 || K == 0)  // no stream-K form: one row, an empty result, or no terms
+    return rd_minplus_gemm(A, lda, B, ldb, C, ldc, M, N, K, min_out, s);
+  SkLayout L;
+  if (!sk_layout(M, N, K, &L)) return RD_ERR_CUDA;
+  const int64_t units = L.tiles * ((K + BK - 1) / BK);
+  if (units * L.grid >= ((int64_t)1 << 32))  // many waves of whole tiles: the one-CTA-per-tile kernel
+    return rd_minplus_gemm(A, lda, B, ldb, C, ldc, M, N, K, min_out, s);
+  if (!work || (reinterpret_cast<uintptr_t>(work) & 255u) != 0) return RD_ERR_ARG;
+  if (work_bytes < L.cnt_bytes + L.part_bytes) return RD_ERR_NOMEM;
+  cudaError_t e = cudaSuccess;
+  if (min_out) {
+    e = launch_fill_i32(min_out, RD_INF, s);
+    if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
+  }
+  GemmParams p{};
+  p.A = A; p.lda = lda; p.B = B; p.ldb = ldb; p.C = C; p.ldc = ldc;
+  p.M = M; p.N = N; p.K = K; p.min_out = min_out; p.diag_out = nullptr;
+  StreamK sk{};
+  sk.gx = (uint32_t)((N + BN - 1) / BN);
+  sk.gy = (uint32_t)((M + BM - 1) / BM);
+  sk.KT = (uint32_t)((K + BK - 1) / BK);
+  sk.U = (uint32_t)units;
+  sk.part = static_cast<uint4*>(work);
+  sk.cnt = reinterpret_cast<uint32_t*>(static_cast<char*>(work) + L.part_bytes);
+  e = set_smem_attr<6>();
+  if (e == cudaSuccess) {
+    minplus_gemm_streamk_kernel<<<(unsigned)L.grid, NT, SMEM_BYTES, s>>>(p, sk);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) { set_cuda_error(e); return RD_ERR_CUDA; }
   return RD_OK;
 }

@@ -114,6 +114,67 @@ def test_minplus_gemm(rd, torch_mod, orc, shape, dist):
     assert mn.item() == want.min()
 
 
+# stream-K: one tile over 7 k-tiles (7 CTAs of one unit each), 9 tiles of 63 k-tiles over 1-2 units per CTA,
+# 128 tiles of 2 k-tiles (every tile split in two), and ragged M, N, K in every position
+SK_SHAPES = SHAPES + [(128, 256, 224), (384, 768, 2000), (2048, 2048, 64), (1024, 1024, 1024), (640, 1100, 3001)]
+
+
+@pytest.mark.parametrize("shape", SK_SHAPES)
+def test_minplus_gemm_streamk(rd, torch_mod, orc, shape):
+    """rd_minplus_gemm_streamk element by element against the oracle, with junk in the padding; the
+    workspace's counters are zero again after the call."""
+    torch = torch_mod
+    from paper_2409_17658_gb300 import inputs
+
+    M, N, K = shape
+    a = inputs.matrix(M, K, seed=21, dist="u32")
+    b = inputs.matrix(K, N, seed=22, dist="u32")
+    A = upload(torch, a, ld=(K + 7) // 8 * 8 + 8, junk=-7)
+    B = upload(torch, b, ld=(N + 7) // 8 * 8 + 16, junk=-7)
+    C = torch.full((M, (N + 7) // 8 * 8), 12345, dtype=torch.int16, device="cuda")
+    mn = torch.zeros(1, dtype=torch.int32, device="cuda")
+    work = rd.minplus_gemm_streamk_workspace(M, N, K)
+    rd.minplus_gemm_streamk(A, B, C, work, M, N, K, min_out=mn)
+    want = orc.minplus_i16(a, b)
+    got = C.cpu().numpy()
+    assert np.array_equal(got[:, :N].astype(np.int32), want)
+    assert np.all(got[:, N:] == 12345)
+    assert mn.item() == want.min()
+    tiles = ((M + 127) // 128) * ((N + 255) // 256)
+    cnt0 = work.numel() - (4 * tiles + 255) // 256 * 256  # the counters follow the partial tiles
+    assert int(work[cnt0:cnt0 + 4 * tiles].view(torch.int32).abs().sum().item()) == 0
+
+
+def test_minplus_gemm_streamk_reuses_its_workspace(rd, torch_mod, orc):
+    """One workspace through products of different shapes on two streams in turn (each call after the
+    previous one), then a short workspace and a misaligned one are refused."""
+    torch = torch_mod
+    from paper_2409_17658_gb300 import inputs
+
+    shapes = [(1024, 1024, 1024), (257, 300, 1500), (2048, 2048, 64), (129, 257, 33), (1024, 1024, 1024)]
+    work = rd.minplus_gemm_streamk_workspace(2048, 2048, 1024)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for i, (M, N, K) in enumerate(shapes):
+        a = inputs.matrix(M, K, seed=31 + i, dist="wide")
+        b = inputs.matrix(K, N, seed=41 + i, dist="wide")
+        A, B = upload(torch, a, ld=(K + 7) // 8 * 8), upload(torch, b, ld=(N + 7) // 8 * 8)
+        C = torch.empty((M, (N + 7) // 8 * 8), dtype=torch.int16, device="cuda")
+        s = streams[i % 2]
+        s.wait_stream(torch.cuda.current_stream())
+        rd.minplus_gemm_streamk(A, B, C, work, M, N, K, stream=s)
+        s.synchronize()
+        assert np.array_equal(C.cpu().numpy()[:, :N].astype(np.int32), orc.minplus_i16(a, b)), (M, N, K)
+    A = torch.zeros((256, 256), dtype=torch.int16, device="cuda")
+    C = torch.empty_like(A)
+    need = rd.minplus_gemm_streamk_work_bytes(256, 256, 256)
+    with pytest.raises(rd.RdError) as e:
+        rd.minplus_gemm_streamk(A, A, C, work[:need - 256])
+    assert e.value.status == rd.RD_ERR_NOMEM
+    with pytest.raises(rd.RdError) as e:
+        rd.minplus_gemm_streamk(A, A, C, work[16:])
+    assert e.value.status == rd.RD_ERR_ARG
+
+
 @pytest.mark.parametrize("shape", [(1, 300, 1000), (70, 90, 130), (257, 1000, 511), (1030, 129, 2000)])
 def test_minplus_gemm_host(rd, torch_mod, orc, shape):
     """The product through the host-buffer entry point: host strides wider than the rows, pinned and
