@@ -9,7 +9,7 @@ import math
 import numpy as np
 import pytest
 
-from conftest import oracle_m9, read_golden
+from conftest import oracle_first_repeat, oracle_m9, read_golden
 
 pytestmark = pytest.mark.gpu
 
@@ -481,7 +481,8 @@ def test_power_sparse_m9_equals_dense(rd, torch_mod, orc, R):
 # ---------------------------------------------------------------- f3: m = 10 (N = 64769)
 
 def test_power_m10(rd, torch_mod, orc):
-    """m = 10 has no Table 2 row.  What the paper fixes: gamma = 22n/5 for n = 0 mod 5, n >= 10
+    """m = 10 has no Table 2 row.  The oracle's stored first repeat and gamma[1..j] (its row-streamed search)
+    are compared exactly.  What the paper fixes: gamma = 22n/5 for n = 0 mod 5, n >= 10
     (Cor. 12) and n = 5 (Remark 13), gamma >= ceil(22n/5) for n >= 10 (Theorem 11); the path
     DP gives n <= 7; sampled rows of the resident powers are checked against the oracle."""
     torch = torch_mod
@@ -495,6 +496,9 @@ def test_power_m10(rd, torch_mod, orc):
     r = rd.power_until_periodic_sparse(A, n, plan, kmax, work)
     assert r["found"]
     g = r["gamma"]
+    o = oracle_first_repeat(10)  # the oracle's row-streamed first-repeat search
+    assert (r["k"], r["p"], r["q"], r["j"]) == (o["k"], o["p"], o["q"], o["j"])
+    assert [int(x) for x in g[1:r["j"] + 1]] == o["gamma"][1:o["j"] + 1]
 
     def gamma(nn):
         if nn <= r["j"]:

@@ -8,7 +8,7 @@ period search; seeded operands come from paper_2409_17658_gb300.inputs.
 import numpy as np
 import pytest
 
-from conftest import oracle_m9, read_golden
+from conftest import oracle_first_repeat, oracle_m9, read_golden
 
 pytestmark = pytest.mark.gpu
 
@@ -248,7 +248,8 @@ def test_power_split_m9(rd, torch_mod, orc):
 
 
 def test_power_split_m10(rd, torch_mod, orc):
-    """m = 10 (N = 64769): Cor. 12 (gamma = 22n/5 for n = 0 mod 5, n >= 10), Remark 13 (n = 5),
+    """m = 10 (N = 64769): the oracle's first repeat and gamma[1..j] (its row-streamed search, stored), Cor. 12
+    (gamma = 22n/5 for n = 0 mod 5, n >= 10), Remark 13 (n = 5),
     Theorem 11's lower bound, the path DP for n <= 7, and sampled rows of the resident powers."""
     torch = torch_mod
     m, kmax = 10, 48
@@ -259,6 +260,9 @@ def test_power_split_m10(rd, torch_mod, orc):
     r = rd.power_until_periodic_split(A, plan, kmax, work)
     assert r["found"]
     g = r["gamma"]
+    o = oracle_first_repeat(10)  # the oracle's row-streamed first-repeat search
+    assert (r["k"], r["p"], r["q"], r["j"]) == (o["k"], o["p"], o["q"], o["j"])
+    assert [int(x) for x in g[1:r["j"] + 1]] == o["gamma"][1:o["j"] + 1]
 
     def gamma(nn):
         if nn <= r["j"]:

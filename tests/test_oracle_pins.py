@@ -12,7 +12,7 @@ import os
 import numpy as np
 import pytest
 
-from conftest import oracle_m9, read_golden
+from conftest import oracle_first_repeat, oracle_m9, read_golden
 
 INF = 0x3FFFFFFFFFFFFFFF
 LETTERS = "abcd"
@@ -304,13 +304,36 @@ def test_oracle_m9_golden_against_the_paper(orc):
         assert o["gamma"][n] == orc.row_dp(9, n), n
 
 
-@pytest.mark.skipif(not os.environ.get("RD_ORACLE_M9"), reason="about 5 minutes on 8 cores; set RD_ORACLE_M9=1")
-def test_oracle_m9_golden_regenerates(orc):
-    """The stored m = 9 values are the oracle's: the row-streamed search run again gives the same file."""
-    o = oracle_m9()
-    s = orc.power_until_periodic_rows(9, kmax=len(o["gamma"]) - 1)
+@pytest.mark.parametrize("m", [9, 10])
+def test_oracle_golden_regenerates(orc, m):
+    """The stored values are the oracle's: the row-streamed search run again gives the same file (m = 9 takes
+    about 5 minutes on 8 cores, m = 10 about 95; set RD_ORACLE_M9=1 or RD_ORACLE_M10=1)."""
+    if not os.environ.get(f"RD_ORACLE_M{m}"):
+        pytest.skip(f"set RD_ORACLE_M{m}=1 to rerun the oracle's m = {m} search")
+    o = oracle_first_repeat(m)
+    s = orc.power_until_periodic_rows(m, kmax=len(o["gamma"]) - 1)
     assert s["found"] and (s["k"], s["p"], s["q"], s["j"]) == (o["k"], o["p"], o["q"], o["j"])
     assert [int(x) for x in s["gamma"][1:]] == o["gamma"][1:]
+
+
+def test_oracle_m10_golden_against_the_paper(orc):
+    """The stored m = 10 result of the oracle (no Table 2 row) against what the paper fixes: the conjectured
+    period 5 and step 2(m + 1) = 22 (Sec. 5), Cor. 12 (gamma = 22n/5 for n = 0 mod 5, n >= 10), Remark 13
+    (n = 5), Theorem 11's lower bound 22n/5 for n >= 10, and the path DP for small n."""
+    o = oracle_first_repeat(10)
+    assert (o["p"], o["q"]) == (5, 22)
+    assert o["j"] == o["k"] + o["p"]
+    g = o["gamma"]
+    assert g[5] == 22
+    for n in range(10, o["j"] + 1):
+        assert 5 * g[n] >= 22 * n, n
+        if n % 5 == 0:
+            assert 5 * g[n] == 22 * n, n
+    for n in range(3, 6):
+        assert g[n] == orc.row_dp(10, n), n
+    # the relation carries the sequence on: A^(k+p) = q (x) A^k gives gamma(n + p) = gamma(n) + q for n >= k
+    for n in range(o["k"], o["j"] - o["p"] + 1):
+        assert g[n + o["p"]] == g[n] + o["q"], n
 
 
 def test_lemma2_holds_beyond_the_repeat(orc):
