@@ -269,7 +269,7 @@ def time_to_period(rd, torch, ms: list[int], with_oracle: bool) -> dict:
                 entry["oracle_s"] = time.perf_counter() - t0
                 entry["oracle_matches"] = bool(o["found"] and (o["k"], o["p"], o["q"]) == (r["k"], r["p"], r["q"]))
             else:
-                rows = 16 if m <= 9 else 4
+                rows = max(16, oracle.threads())  # one row per host thread at least, so every core works
                 t0 = time.perf_counter()
                 oracle.power_rows(m, np.arange(rows), r["j"])
                 dt_o = time.perf_counter() - t0
