@@ -727,6 +727,7 @@ def main() -> None:
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timings")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-products leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the query-server leg")
+    ap.add_argument("--streamk", action="store_true", help="with --gemm-only: time rd_minplus_gemm_streamk")
     ap.add_argument("--gemm-only", type=int, default=0, metavar="N",
                     help="time only the product at size N (used for profiler captures)")
     ap.add_argument("--sparse-only", type=int, default=0, metavar="M",
@@ -824,8 +825,18 @@ def main() -> None:
         if dist is not None:
             dist.barrier()
 
+    if args.gemm_only and args.streamk:
+        sk_work = rd.minplus_gemm_streamk_workspace(n, n, n)
+
+        def product():
+            rd.minplus_gemm_streamk(A, B, C, sk_work, min_out=mn)
+    else:
+
+        def product():
+            rd.minplus_gemm(A, B, C, min_out=mn)
+
     for _ in range(max(args.warmup, 3)):
-        rd.minplus_gemm(A, B, C, min_out=mn)
+        product()
     torch.cuda.synchronize()
     # the roofline's denominator, measured on this GPU (a 17 ms register-resident DPX loop)
     with ClockSampler(local) as peak_clocks:
@@ -842,7 +853,7 @@ def main() -> None:
         start.record(stream)
         for i in range(args.steps):
             ev[i][0].record(stream)
-            rd.minplus_gemm(A, B, C, min_out=mn)
+            product()
             ev[i][1].record(stream)
         stop.record(stream)
         torch.cuda.synchronize()
@@ -854,7 +865,8 @@ def main() -> None:
     clk = clocks.summary()
     if args.gemm_only:
         if rank == 0:
-            print(json.dumps({"gemm_only": n, "steps": args.steps, "ms_per_launch": per_launch_ms,
+            print(json.dumps({"gemm_only": n, "streamk": bool(args.streamk), "steps": args.steps,
+                              "ms_per_launch": per_launch_ms,
                               "gops": ops_per_step / (per_launch_ms * 1e-3) / 1e9, "clocks": clk}))
         return
     a = A.cpu().numpy()
