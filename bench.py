@@ -568,7 +568,11 @@ def batched_products(rd, torch, count: int = 64, seed: int = 4) -> dict:
     out["periods_m1_to_9"] = {"sequential_s": timings["sequential"], "together_graph_s": timings["together_graph"],
                               "together_launches_per_phase_s": timings["together_graph_launches_per_phase"],
                               "speedup": timings["sequential"] / timings["together_graph"],
-                              "launches_per_step": 1,
+                              # per step: one multi_step_kernel launch for the sparse runs (m = 1..7), and per
+                              # row-split run (m = 8, 9) its two passes, the normaliser check, finalize and compare
+                              "launches_per_step": 1 + 5 * sum(1 for run in runs if "info" in run[2]),
+                              "launches_how": "sparse runs m = 1..7: one multi_step_kernel launch; row-split runs "
+                                              "m = 8, 9: two passes + normaliser check + finalize + compare each",
                               "same_results": (timings["sequential_triples"] == timings["together_graph_triples"] ==
                                                timings["together_graph_launches_per_phase_triples"]),
                               "triples": timings["together_graph_triples"]}
