@@ -569,10 +569,10 @@ def batched_products(rd, torch, count: int = 64, seed: int = 4) -> dict:
                               "together_launches_per_phase_s": timings["together_graph_launches_per_phase"],
                               "speedup": timings["sequential"] / timings["together_graph"],
                               # per step: one multi_step_kernel launch for the sparse runs (m = 1..7), and per
-                              # row-split run (m = 8, 9) its two passes, the normaliser check, finalize and compare
-                              "launches_per_step": 1 + 5 * sum(1 for run in runs if "info" in run[2]),
+                              # row-split run (m = 8, 9) its two passes, finalize and compare
+                              "launches_per_step": 1 + 4 * sum(1 for run in runs if "info" in run[2]),
                               "launches_how": "sparse runs m = 1..7: one multi_step_kernel launch; row-split runs "
-                                              "m = 8, 9: two passes + normaliser check + finalize + compare each",
+                                              "m = 8, 9: two passes + finalize + compare each",
                               "same_results": (timings["sequential_triples"] == timings["together_graph_triples"] ==
                                                timings["together_graph_launches_per_phase_triples"]),
                               "triples": timings["together_graph_triples"]}

@@ -162,7 +162,9 @@ cudaError_t enqueue_phase_step(int R, const MultiParams& mp, int grid, cudaStrea
   cudaError_t e = launch_multi_product(R, mp, s);
   if (e != cudaSuccess) return e;
   const dim3 g((unsigned)grid, (unsigned)mp.count);
-  multi_normalise_kernel<false><<<g, 256, 0, s>>>(mp);
+  bool all_normalised = true;  // row-split products that wrote the normalised power need no normaliser pass
+  for (int i = 0; i < mp.count; ++i) all_normalised = all_normalised && mp.r[i].normalised;
+  if (!all_normalised) multi_normalise_kernel<false><<<g, 256, 0, s>>>(mp);
   multi_finalize_kernel<<<dim3(1, (unsigned)mp.count), 32, 0, s>>>(mp);
   multi_compare_kernel<<<g, 256, 0, s>>>(mp);
   return cudaGetLastError();

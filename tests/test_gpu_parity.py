@@ -145,6 +145,28 @@ def test_minplus_gemm_streamk(rd, torch_mod, orc, shape):
     assert int(work[cnt0:cnt0 + 4 * tiles].view(torch.int32).abs().sum().item()) == 0
 
 
+@pytest.mark.parametrize("shape", [(0, 16, 16), (16, 0, 16), (16, 16, 0), (300, 257, 0)])
+def test_minplus_gemm_streamk_degenerate(rd, torch_mod, shape):
+    """Empty products through the stream-K entry point: no rows or columns writes nothing, no terms (K = 0)
+    gives an all-RD_INF C and min_out = RD_INF; the workspace is not touched."""
+    torch = torch_mod
+    M, N, K = shape
+    A = torch.zeros((max(M, 1), max((K + 7) // 8 * 8, 8)), dtype=torch.int16, device="cuda")
+    B = torch.zeros((max(K, 1), max((N + 7) // 8 * 8, 8)), dtype=torch.int16, device="cuda")
+    C = torch.full((max(M, 1), max((N + 7) // 8 * 8, 8)), 77, dtype=torch.int16, device="cuda")
+    mn = torch.zeros(1, dtype=torch.int32, device="cuda")
+    work = rd.minplus_gemm_streamk_workspace(max(M, 1), max(N, 1), max(K, 1))
+    rd.minplus_gemm_streamk(A, B, C, work, M, N, K, min_out=mn)
+    torch.cuda.synchronize()
+    got = C.cpu().numpy()
+    if M > 0 and N > 0:
+        assert np.all(got[:M, :N] == I16_INF)
+    else:
+        assert np.all(got == 77)
+    assert mn.item() == int(I16_INF)
+    assert int(work.sum().item()) == 0
+
+
 def test_minplus_gemm_streamk_reuses_its_workspace(rd, torch_mod, orc):
     """One workspace through products of different shapes on two streams in turn (each call after the
     previous one), then a short workspace and a misaligned one are refused."""
