@@ -36,6 +36,7 @@
 // for balanced splits: the CTA stages them in shared memory together with the rows, so the folding
 // loop reads nothing but shared memory.  When they do not fit (very unbalanced splits), the kernel
 // reads them from global memory instead.
+#include <initializer_list>
 #include <mutex>
 
 #include "power_dev.cuh"
@@ -227,7 +228,7 @@ bool make_layout(int m, int j, Layout* L) {
   L->l2 = take((size_t)L->l2B * 2);
   L->go2 = take((size_t)L->nPi * (size_t)L->nG2 * 4 * 4);
   L->ord2 = take((size_t)L->nPi * (size_t)L->nG2 * 2);
-  L->counters = take(8 * 4);
+  L->counters = take(32 * 4);  // [0, 8): counters of the build; [16, 24): the readback stage
   L->bytes = off;
   return true;
 }
@@ -1140,6 +1141,23 @@ cudaError_t read_i32(const int32_t* dev, int32_t* host, int n, cudaStream_t s) {
   return e;
 }
 
+// Up to 8 scattered device int32 values gathered into one readback (one host round trip instead of n).
+struct Gather8 {
+  const int32_t* src[8];
+  int n;
+};
+__global__ void gather_i32_kernel(Gather8 g, int32_t* dst) {
+  if ((int)threadIdx.x < g.n) dst[threadIdx.x] = *g.src[threadIdx.x];
+}
+cudaError_t read_gathered_i32(std::initializer_list<const int32_t*> srcs, int32_t* stage_dev, int32_t* host,
+                              cudaStream_t s) {
+  Gather8 g{};
+  for (const int32_t* p : srcs) g.src[g.n++] = p;
+  gather_i32_kernel<<<1, 32, 0, s>>>(g, stage_dev);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? read_i32(stage_dev, host, g.n, s) : e;
+}
+
 }  // namespace
 
 bool split_width_fits(int W, int max_slots) { return valid_w(W, max_slots); }
@@ -1199,7 +1217,8 @@ extern "C" rd_status rd_split_plan(int m, int j, void* plan_dev, size_t plan_byt
   const int32_t* totals[6] = {at<int32_t>(P, L.rankR) + n5j,         at<int32_t>(P, L.rankS) + n5h,
                               at<int32_t>(P, L.rankPi) + ipow(4, j), at<int32_t>(P, L.rankPhi) + ipow(4, h),
                               at<int32_t>(P, L.rankG1) + ipow(4, j - 1), at<int32_t>(P, L.rankG2) + ipow(4, h - 1)};
-  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = read_i32(totals[i], &cnt[i], 1, s);
+  int32_t* stage = counters + 16;
+  e = read_gathered_i32({totals[0], totals[1], totals[2], totals[3], totals[4], totals[5]}, stage, cnt, s);
   if (e != cudaSuccess) return fail(e);
   const int64_t n_rho = cnt[0], n_sigma = cnt[1];
   // the type counts are within their bounds, and the letter words counted are the correct words
@@ -1236,11 +1255,10 @@ extern "C" rd_status rd_split_plan(int m, int j, void* plan_dev, size_t plan_byt
                                             at<int32_t>(P, L.fstart2), counters + 1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(e);
-  int32_t c2[2] = {0, 0}, x_rows = 0;
-  e = read_i32(counters, c2, 2, s);
-  if (e == cudaSuccess) e = read_i32(at<int32_t>(P, L.xrank) + nx, &x_rows, 1, s);
+  int32_t c3[3] = {0, 0, 0};
+  e = read_gathered_i32({counters, counters + 1, at<int32_t>(P, L.xrank) + nx}, stage, c3, s);
   if (e != cudaSuccess) return fail(e);
-  const int32_t slots1 = c2[0], slots2 = c2[1];
+  const int32_t slots1 = c3[0], slots2 = c3[1], x_rows = c3[2];
   if (slots1 < 1 || slots1 > L.nPi || slots2 < 1 || slots2 > n_sigma || x_rows < 1) return RD_ERR_RANGE;
 
   GroupArgs g1{};
@@ -1269,19 +1287,19 @@ extern "C" rd_status rd_split_plan(int m, int j, void* plan_dev, size_t plan_byt
   scan_i32_kernel<<<1, 1024, 0, s>>>(at<int32_t>(P, L.gls2), nrec2 * kRec);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(e);
-  int32_t tot[3] = {0, 0, 0};
-  e = read_i32(at<int32_t>(P, L.gls1) + nrec1 * kRec, &tot[0], 1, s);
-  if (e == cudaSuccess) e = read_i32(at<int32_t>(P, L.gls2) + nrec2 * kRec, &tot[1], 1, s);
-  if (e == cudaSuccess) e = read_i32(counters + 4, &tot[2], 1, s);
+  // the longest fiber lists (read only from the scanned counts, so safe to take before the checks below)
+  fiber_list_max_kernel<<<grid_for(n_sigma), 256, 0, s>>>(at<int32_t>(P, L.gls1), n_sigma, L.nG1, counters + 2);
+  fiber_list_max_kernel<<<grid_for(L.nPi), 256, 0, s>>>(at<int32_t>(P, L.gls2), L.nPi, L.nG2, counters + 3);
+  int32_t tot[5] = {0, 0, 0, 0, 0};
+  e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = read_gathered_i32({at<int32_t>(P, L.gls1) + nrec1 * kRec, at<int32_t>(P, L.gls2) + nrec2 * kRec, counters + 4,
+                           counters + 2, counters + 3},
+                          stage, tot, s);
   if (e != cudaSuccess) return fail(e);
   // a target set outside the 7 would be a slip in the rules above: refuse the plan
   if (tot[0] > L.l1B || tot[1] > L.l2B || tot[2] != 0) return RD_ERR_RANGE;
-  fiber_list_max_kernel<<<grid_for(n_sigma), 256, 0, s>>>(at<int32_t>(P, L.gls1), n_sigma, L.nG1, counters + 2);
-  fiber_list_max_kernel<<<grid_for(L.nPi), 256, 0, s>>>(at<int32_t>(P, L.gls2), L.nPi, L.nG2, counters + 3);
-  int32_t lm[2] = {0, 0};
-  e = cudaGetLastError();
-  if (e == cudaSuccess) e = read_i32(counters + 2, lm, 2, s);
-  if (e != cudaSuccess) return fail(e);
+  const int32_t lm[2] = {tot[3], tot[4]};
   const int w1 = choose_w(slots1, (int)L.nG1, lm[0], true), w2 = choose_w(slots2, (int)L.nG2, lm[1], false);
   if (w1 == 0 || w2 == 0) return RD_ERR_ARG;  // a fiber does not fit in shared memory
   group_lists_kernel<true><<<grid_for(nrec1), 256, 0, s>>>(g1, at<int32_t>(P, L.gls1), at<uint16_t>(P, L.l1), nullptr);
