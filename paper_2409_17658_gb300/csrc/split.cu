@@ -1152,6 +1152,7 @@ __global__ void gather_i32_kernel(Gather8 g, int32_t* dst) {
 cudaError_t read_gathered_i32(std::initializer_list<const int32_t*> srcs, int32_t* stage_dev, int32_t* host,
                               cudaStream_t s) {
   Gather8 g{};
+  if (srcs.size() > 8) return cudaErrorInvalidValue;
   for (const int32_t* p : srcs) g.src[g.n++] = p;
   gather_i32_kernel<<<1, 32, 0, s>>>(g, stage_dev);
   const cudaError_t e = cudaGetLastError();
