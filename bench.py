@@ -394,6 +394,35 @@ def run_split_only(rd, torch, args) -> None:
                       "GBps": moved / (ms * 1e-3) / 1e9, "frac_of_measured_hbm": moved / (ms * 1e-3) / 1e9 / HBM_GBS}))
 
 
+def run_search_only(rd, torch, args) -> None:
+    """The period search with the row-split step at m = M, repeated (--tune: the plan's launch shape from the
+    autotuner first): the kernel sequence of one power step, for profiling."""
+    m = args.search_only
+    A, n = rd.transfer_matrix(m)
+    plan = rd.split_plan(m, x_ld=A.stride(0))
+    if args.tune:
+        P = torch.empty_like(A)
+        C = torch.empty_like(A)
+        rd.split_minplus(plan, A, P)
+        rd.tune_split(plan, P, C, reps=2)
+        del P, C
+    kmax = 48
+    work = rd.power_workspace(n, A.stride(0), kmax, 8)
+    for _ in range(args.warmup):
+        rd.power_until_periodic_split(A, plan, kmax, work)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = rd.power_until_periodic_split(A, plan, kmax, work)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    info = plan["info"]
+    print(json.dumps({"search_only_m": m, "N": n, "k": r["k"], "p": r["p"], "q": r["q"], "powers": r["j"],
+                      "shape": [info.w1, info.k1, info.w2, info.k2], "s_per_search": float(np.median(times)),
+                      "ms_per_power": float(np.median(times)) * 1e3 / r["j"]}))
+
+
 def gemv_leg(rd, torch, B, n: int, reps: int = 20) -> dict:
     """The matrix-vector form of the synthetic workload: y = x (x) B at N = 16384, against HBM bandwidth."""
     from paper_2409_17658_gb300 import inputs
@@ -741,7 +770,10 @@ def main() -> None:
                     help="time only the one-row product against an N x N operand (profiling aid)")
     ap.add_argument("--split-only", type=int, default=0, metavar="M",
                     help="time only the row-split product at m = M (profiling aid)")
-    ap.add_argument("--tune", action="store_true", help="with --split-only: run the autotuner on the plan first")
+    ap.add_argument("--search-only", type=int, default=0, metavar="M",
+                    help="run only the row-split period search at m = M (profiling aid)")
+    ap.add_argument("--tune", action="store_true",
+                    help="with --split-only or --search-only: run the autotuner on the plan first")
     ap.add_argument("--batched-only", action="store_true", help="time only the 64-product batch (profiling aid)")
     ap.add_argument("--build-only", type=int, default=0, metavar="M",
                     help="time only the A(G) builder at m = M (profiling aid)")
@@ -770,6 +802,8 @@ def main() -> None:
         return run_sparse_only(rd, torch, args)
     if args.split_only:
         return run_split_only(rd, torch, args)
+    if args.search_only:
+        return run_search_only(rd, torch, args)
     if args.batched_only:
         return run_batched_only(rd, torch, args)
     if args.multi_only:
