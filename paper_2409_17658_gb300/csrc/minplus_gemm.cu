@@ -831,9 +831,12 @@ struct SkLayout {
 };
 bool sk_layout(int64_t M, int64_t N, int64_t K, SkLayout* L) {
   int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
-                                                cudaSuccess || sms < 1)
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess || sms < 1) {
+    set_cuda_error(e != cudaSuccess ? e : cudaErrorInvalidDevice);
     return false;
+  }
   const int64_t gx = (N + BN - 1) / BN, gy = (M + BM - 1) / BM, KT = (K + BK - 1) / BK;
   L->tiles = gx * gy;
   const int64_t U = L->tiles * KT;
