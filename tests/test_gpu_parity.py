@@ -367,6 +367,19 @@ def test_power_not_found_within_kmax(rd, torch_mod, orc):
     assert np.array_equal(r["gamma"][1:10], orc.gamma_direct(3, 9)[1:10])
 
 
+@pytest.mark.parametrize("m,kmax", [(5, 20), (6, 7)])
+def test_power_not_found_within_kmax_step_kernels(rd, torch_mod, orc, m, kmax):
+    """The dense search through the step kernels (N > 128, blocks of steps queued ahead of the host's check)
+    stopped by kmax before its repeat: RD_NOT_FOUND, gamma[1..kmax] equal to the oracle's, nothing past kmax."""
+    A, n = rd.transfer_matrix(m)
+    assert n > 128
+    r, _ = run_power(rd, torch_mod, A, n, kmax=kmax, slots=8)
+    assert r["status"] == rd.RD_NOT_FOUND and not r["found"]
+    want = orc.power_until_periodic(m, kmax=kmax)
+    assert not want["found"]
+    assert np.array_equal(r["gamma"][1:kmax + 1], want["gamma"][1:kmax + 1])
+
+
 def test_power_ring_too_short(rd, torch_mod):
     A, n = rd.transfer_matrix(2)  # period 4 needs at least 5 slots
     work = rd.power_workspace(n, A.stride(0), 40, 3)

@@ -198,6 +198,24 @@ def test_power_split_matches_oracle(rd, torch_mod, orc, m):
             assert np.array_equal(pk, to_i16(np.where(want == INF64, INF64, want - fin.min()))), k
 
 
+@pytest.mark.parametrize("m,kmax", [(5, 17), (5, 20), (7, 9), (7, 25)])
+def test_power_split_not_found_within_kmax(rd, torch_mod, orc, m, kmax):
+    """The row-split search stopped by kmax one power short of its repeat (and far short of it): RD_NOT_FOUND,
+    with gamma[1..kmax] equal to the oracle's, and the same workspace then finds the relation."""
+    torch = torch_mod
+    A, n = rd.transfer_matrix(m)
+    plan = rd.split_plan(m)
+    work = rd.power_workspace(n, A.stride(0), 48, 8)
+    r = rd.power_until_periodic_split(A, plan, kmax, work)
+    assert r["status"] == rd.RD_NOT_FOUND and not r["found"]
+    want = orc.power_until_periodic(m, kmax=48)["gamma"]
+    assert [int(x) for x in r["gamma"][1:kmax + 1]] == [int(x) for x in want[1:kmax + 1]]
+    r2 = rd.power_until_periodic_split(A, plan, 48, work)
+    assert r2["found"] and r2["j"] > kmax
+    del work, plan, A
+    torch.cuda.empty_cache()
+
+
 def test_power_split_m8_matches_oracle(rd, torch_mod, orc):
     A, n = rd.transfer_matrix(8)
     plan = rd.split_plan(8)
