@@ -380,6 +380,21 @@ def test_power_not_found_within_kmax_step_kernels(rd, torch_mod, orc, m, kmax):
     assert np.array_equal(r["gamma"][1:kmax + 1], want["gamma"][1:kmax + 1])
 
 
+@pytest.mark.parametrize("R", [1, 2])
+def test_power_sparse_not_found_within_kmax(rd, torch_mod, orc, R):
+    """The dense x sparse search stopped by kmax before its repeat (m = 6, j = 24): RD_NOT_FOUND with
+    gamma[1..kmax] equal to the oracle's; the same workspace then finds (19, 5, 14)."""
+    A, n = rd.transfer_matrix(6)
+    plan = rd.sparse_plan(A, n, n, R)
+    work = rd.power_workspace(n, A.stride(0), 48, 8)
+    r = rd.power_until_periodic_sparse(A, n, plan, 20, work)
+    assert r["status"] == rd.RD_NOT_FOUND and not r["found"]
+    want = orc.power_until_periodic(6, kmax=20)
+    assert np.array_equal(r["gamma"][1:21], want["gamma"][1:21])
+    r2 = rd.power_until_periodic_sparse(A, n, plan, 48, work)
+    assert (r2["k"], r2["p"], r2["q"]) == (19, 5, 14)
+
+
 def test_power_ring_too_short(rd, torch_mod):
     A, n = rd.transfer_matrix(2)  # period 4 needs at least 5 slots
     work = rd.power_workspace(n, A.stride(0), 40, 3)
@@ -658,6 +673,30 @@ def test_power_multi_equals_single_runs(rd, torch_mod, orc, graph_steps):
             o = orc.power_until_periodic(m, kmax=kmax)
             assert (r["k"], r["p"], r["q"]) == (o["k"], o["p"], o["q"]), m
     assert (res[8]["k"], res[8]["p"], res[8]["q"]) == (22, 5, 20)
+
+
+@pytest.mark.parametrize("graph_steps", [0, 8])
+def test_power_multi_mixed_found_and_not_found(rd, torch_mod, orc, graph_steps):
+    """kmax = 15 lets m = 1..3 find their repeats (j = 9, 10, 15) while m = 4..8 run out: each run's status, and its
+    relation and gamma up to j (found) or kmax (not found), equal the oracle's; m = 8 runs with the row split."""
+    kmax = 15
+    runs = []
+    for m in range(1, 9):
+        A, n = rd.transfer_matrix(m)
+        plan = rd.split_plan(m, x_ld=A.stride(0)) if m == 8 else rd.sparse_plan(A, n, n, 2)
+        runs.append((A, n, plan, rd.power_workspace(n, A.stride(0), kmax, 8)))
+    res = rd.power_until_periodic_multi(runs, 2, kmax, graph_steps=graph_steps)
+    for m, r in zip(range(1, 9), res):
+        o = orc.power_until_periodic(m, kmax=kmax) if m <= 7 else None
+        if m == 8:
+            assert r["status"] == rd.RD_NOT_FOUND
+            continue
+        assert r["found"] == o["found"], m
+        if o["found"]:
+            assert r["status"] == rd.RD_OK and (r["k"], r["p"], r["q"]) == (o["k"], o["p"], o["q"]), m
+        else:
+            assert r["status"] == rd.RD_NOT_FOUND, m
+        assert np.array_equal(r["gamma"][1:o["j"] + 1], o["gamma"][1:o["j"] + 1]), m
 
 
 def test_power_multi_wait_runs_out(rd, torch_mod, orc):
