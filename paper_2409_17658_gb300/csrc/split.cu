@@ -649,8 +649,8 @@ __host__ __device__ inline PassSmem pass_smem_layout(int max_slots, int n_groups
   return p;
 }
 
-// One (fiber f, slab group) of a pass: the body of split_pass_kernel, also run as an item of the multi-run
-// step kernel.  sm: the dynamic shared memory (pass_smem bytes).
+// One (fiber f, slab group) of a pass: the body of split_pass_kernel.  sm: the dynamic shared memory
+// (pass_smem bytes).
 template <int W, bool FIRST, bool RING, bool STAGED>
 __device__ __forceinline__ void split_pass_body(const SplitPass& a, const int64_t f, const int64_t slab_group,
                                                 uint4* sm) {
