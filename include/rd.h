@@ -517,6 +517,37 @@ rd_status rd_power_until_periodic_multi_bounded(rd_power_run *runs, int count, i
                                                 uint32_t wait_ms, int32_t stall_run, cudaStream_t s);
 
 /*
+ * Relation records: checkpoint and resume of the per-m results.  What the
+ * period search yields for A(G) of P_m -- the first repeat A^(k+p) = q (x) A^k
+ * (Lemma 2, Algorithm 2) and gamma[n] = min diag(A^n) for n <= k + p
+ * (Corollary 6) -- fixes gamma_R(P_m box C_n) for every n through the solution
+ * of the finite-difference equation of Prop. 7, in a few hundred bytes.  A
+ * record exported by one process can be imported by another, which then answers
+ * every n of that m on the host with no device work (the search costs about
+ * 0.35 s and 87 GB of device memory at m = 10, 9 s and 225 GB at m = 11).
+ * Records describe the transfer matrix of Sec. 4.A (rd_build_transfer), not the
+ * Appendix variant.
+ *   m      1..RD_MAX_M.
+ *   found  1: A^(k+p) = q (x) A^k with the smallest k + p; 0: no relation with
+ *          k + p <= j (then k = p = 0, q = 0).
+ *   k, p   found: k >= 1, p >= 1.
+ *   q      found: gamma(n + p) - gamma(n) for every n >= k.
+ *   j      gamma[1..j] are recorded: j = k + p when found, else the kmax
+ *          searched; 1 <= j <= RD_RELATION_MAX_J.
+ * The gamma array that goes with a record has j + 1 entries; gamma[0] is not
+ * used (RD_GAMMA_UNSET on export, ignored on import).
+ */
+#define RD_RELATION_MAX_J (1 << 20)
+typedef struct {
+  int32_t m;
+  int32_t found;
+  int32_t k, p;
+  int64_t q;
+  int32_t j;
+  int32_t reserved; /* 0 */
+} rd_relation_t;
+
+/*
  * Query server with continuous batching (for many gamma_R(P_m box C_n) queries).
  * A worker thread on the device current at creation keeps one period-search job
  * per m that has been asked for and is not settled yet.  Each step advances all
@@ -552,6 +583,16 @@ rd_status rd_server_wait(rd_server *sv, int count, const uint64_t *tickets, doub
                          int32_t *status, double *latency_s);
 
 rd_status rd_server_stats(rd_server *sv, rd_server_stats_t *out);
+/* rd_server_export -- the server's final record for m (rd_relation_t above): RD_OK with
+ * *rel filled (gamma[0..j] too when gamma is not NULL and cap >= rel->j + 1, else
+ * RD_ERR_ARG), RD_NOT_FOUND when the server holds no final record for m (never searched,
+ * or its search still running), or the status its search failed with.  No CUDA call. */
+rd_status rd_server_export(rd_server *sv, int m, rd_relation_t *rel, int64_t *gamma, int64_t cap);
+/* rd_server_import -- warm start: installs a record (checked as by rd_gamma_R_import, else
+ * RD_ERR_ARG) as the server's final record for rel->m.  Queries routed after the call are
+ * answered from it on the host, with no job; a search already running for that m still
+ * completes, and its own record then replaces the imported one. */
+rd_status rd_server_import(rd_server *sv, const rd_relation_t *rel, const int64_t *gamma);
 
 /* rd_server_destroy -- stop the worker, free its device memory; unanswered tickets are dropped. */
 rd_status rd_server_destroy(rd_server *sv);
@@ -723,6 +764,30 @@ rd_status rd_gamma_R(int m, int64_t n, int64_t *out);
 /* rd_gamma_R_clear -- forgets every cached m, so the next rd_gamma_R(m, .) runs its period search again
  * (a cold start, e.g. for timing).  Thread-safe; waits for a search in progress. */
 rd_status rd_gamma_R_clear(void);
+
+/*
+ * rd_gamma_R_export -- the record rd_gamma_R holds for m, running the period
+ * search first when m is not cached (as rd_gamma_R does; same devices, memory
+ * and errors).  *rel is filled on RD_OK; gamma (host, may be NULL to learn
+ * rel->j first) receives gamma[0..j] and needs cap >= rel->j + 1, else
+ * RD_ERR_ARG (with *rel filled).  Thread-safe.
+ */
+rd_status rd_gamma_R_export(int m, rd_relation_t *rel, int64_t *gamma, int64_t cap);
+
+/*
+ * rd_gamma_R_import -- installs a record (for example one saved by an earlier
+ * process) as rd_gamma_R's cache entry for rel->m, replacing any entry; later
+ * rd_gamma_R(rel->m, n) calls answer from it with no device work.  No CUDA call.
+ * The record is checked against what every transfer-matrix record satisfies,
+ * else RD_ERR_ARG and the cache is unchanged:
+ *   the fields are in the ranges above;
+ *   0 <= gamma[n] <= 2 m n for n = 1..j (labels are non-negative, and the word
+ *   of m letters a, which follows itself, gives a closed walk of label 2 m n);
+ *   found: gamma[k + p] = gamma[k] + q (min diag(q (x) A^k) = q + min diag A^k).
+ * It cannot tell a wrong record that passes these checks: the caller vouches
+ * for the record's origin.  Thread-safe.
+ */
+rd_status rd_gamma_R_import(const rd_relation_t *rel, const int64_t *gamma);
 
 #ifdef __cplusplus
 }

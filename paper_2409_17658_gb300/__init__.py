@@ -120,6 +120,12 @@ def _lib():
         lib.rd_minplus_gemm_host_work_bytes.restype = st
         lib.rd_minplus_gemm_host.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, vp, sz, vp, vp]
         lib.rd_minplus_gemm_host.restype = st
+        lib.rd_gamma_R_export.argtypes = [ctypes.c_int, vp, vp, i64]
+        lib.rd_gamma_R_import.argtypes = [vp, vp]
+        lib.rd_server_export.argtypes = [vp, ctypes.c_int, vp, vp, i64]
+        lib.rd_server_import.argtypes = [vp, vp, vp]
+        for name in ("rd_gamma_R_export", "rd_gamma_R_import", "rd_server_export", "rd_server_import"):
+            getattr(lib, name).restype = st
         _ = i32
         _LIB = lib
     return _LIB
@@ -305,6 +311,41 @@ def power_until_periodic_multi(runs, R: int, kmax: int, graph_steps: int = 8, st
     return out
 
 
+class Relation(ctypes.Structure):
+    """rd_relation_t: the first repeat A^(k+p) = q (x) A^k of one m and how many gamma values go with it."""
+    _fields_ = [("m", ctypes.c_int32), ("found", ctypes.c_int32), ("k", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("q", ctypes.c_int64), ("j", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def _relation_dict(rel: Relation, gamma: np.ndarray) -> dict:
+    found = bool(rel.found)
+    return dict(m=rel.m, found=found, k=rel.k if found else None, p=rel.p if found else None,
+                q=rel.q if found else None, j=rel.j, gamma=[int(v) for v in gamma[1: rel.j + 1]])
+
+
+def _relation_args(rec: dict):
+    """(Relation, gamma array of j + 1 int64) from a record dict (gamma lists n = 1..j)."""
+    found = bool(rec["found"])
+    g = [int(v) for v in rec["gamma"]]
+    rel = Relation(m=int(rec["m"]), found=1 if found else 0, k=int(rec["k"]) if found else 0,
+                   p=int(rec["p"]) if found else 0, q=int(rec["q"]) if found else 0, j=len(g), reserved=0)
+    if int(rec.get("j", len(g))) != len(g):
+        raise ValueError(f"record for m = {rec['m']}: j = {rec['j']} but {len(g)} gamma values")
+    gamma = np.ascontiguousarray([RD_GAMMA_UNSET] + g, dtype=np.int64)
+    return rel, gamma
+
+
+def _export(call, where: str) -> dict | None:
+    rel = Relation()
+    st = call(ctypes.byref(rel), None, 0)
+    if st == RD_NOT_FOUND and where == "rd_server_export":
+        return None
+    _check(st, where)
+    gamma = np.zeros(rel.j + 1, dtype=np.int64)
+    _check(call(ctypes.byref(rel), gamma.ctypes.data, len(gamma)), where)
+    return _relation_dict(rel, gamma)
+
+
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("answered", ctypes.c_uint64), ("steps", ctypes.c_uint64),
                 ("jobs_admitted", ctypes.c_uint64), ("jobs_completed", ctypes.c_uint64),
@@ -336,6 +377,15 @@ class Server:
         _check(_lib().rd_server_wait(self._h, len(tickets), tickets.ctypes.data, timeout_s, g.ctypes.data,
                                      st.ctypes.data, lat.ctypes.data), "rd_server_wait")
         return g, st, lat
+
+    def export_relation(self, m: int) -> dict | None:
+        """rd_server_export: the server's final record for m as a dict, or None while it has none."""
+        return _export(lambda r, g, c: _lib().rd_server_export(self._h, m, r, g, c), "rd_server_export")
+
+    def import_relation(self, rec: dict) -> None:
+        """rd_server_import: warm start -- queries for rec['m'] are answered from the record."""
+        rel, gamma = _relation_args(rec)
+        _check(_lib().rd_server_import(self._h, ctypes.byref(rel), gamma.ctypes.data), "rd_server_import")
 
     def stats(self) -> dict:
         s = ServerStats()
@@ -666,6 +716,18 @@ def gamma_R(m: int, n: int) -> int:
 def gamma_R_clear() -> None:
     """rd_gamma_R_clear: forget every cached m (the next rd_gamma_R of each m searches again)."""
     _check(_lib().rd_gamma_R_clear(), "rd_gamma_R_clear")
+
+
+def gamma_R_export(m: int) -> dict:
+    """rd_gamma_R_export: dict(m, found, k, p, q, j, gamma) with gamma = [gamma(1), ..., gamma(j)];
+    runs the period search first when m is not cached."""
+    return _export(lambda r, g, c: _lib().rd_gamma_R_export(m, r, g, c), "rd_gamma_R_export")
+
+
+def gamma_R_import(rec: dict) -> None:
+    """rd_gamma_R_import: install a record (as gamma_R_export returns it) as the cache entry of rec['m']."""
+    rel, gamma = _relation_args(rec)
+    _check(_lib().rd_gamma_R_import(ctypes.byref(rel), gamma.ctypes.data), "rd_gamma_R_import")
 
 
 # ---------------------------------------------------------------- allocation helpers (torch owns device memory)

@@ -581,3 +581,66 @@ extern "C" rd_status rd_gamma_R(int m, int64_t n, int64_t* out) {
   *out = c.gamma[(size_t)(c.k + (n - c.k) % c.p)] + c.q * t;
   return RD_OK;
 }
+
+// ---------------------------------------------------------------- relation records (checkpoint / resume)
+
+bool rd::relation_ok(const rd_relation_t* rel, const int64_t* gamma) {
+  if (!rel || !gamma) return false;
+  const int m = rel->m;
+  if (m < 1 || m > RD_MAX_M || rel->j < 1 || rel->j > RD_RELATION_MAX_J) return false;
+  if (rel->found == 1) {
+    if (rel->k < 1 || rel->p < 1 || (int64_t)rel->k + rel->p != rel->j) return false;
+  } else if (rel->found != 0 || rel->k != 0 || rel->p != 0 || rel->q != 0) {
+    return false;
+  }
+  // every label is >= 0, and the word of m a's follows itself with label 2m: 0 <= min diag A^n <= 2mn
+  for (int64_t n = 1; n <= rel->j; ++n)
+    if (gamma[n] < 0 || gamma[n] > 2 * (int64_t)m * n) return false;
+  // min diag (q (x) A^k) = q + min diag A^k
+  if (rel->found == 1 && gamma[rel->j] != gamma[rel->k] + rel->q) return false;
+  return true;
+}
+
+namespace {
+void fill_relation(int m, const Cached& c, rd_relation_t* rel) {
+  *rel = rd_relation_t{};
+  rel->m = m;
+  rel->found = c.found ? 1 : 0;
+  rel->k = c.found ? c.k : 0;
+  rel->p = c.found ? c.p : 0;
+  rel->q = c.found ? c.q : 0;
+  rel->j = c.j;
+}
+}  // namespace
+
+extern "C" rd_status rd_gamma_R_export(int m, rd_relation_t* rel, int64_t* gamma, int64_t cap) {
+  if (m < 1 || m > RD_MAX_M || !rel) return RD_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  Cached& c = g_cache[m];
+  if (!c.valid) {
+    const rd_status rc = compute_cached(m, &c);
+    if (rc != RD_OK) return rc;
+  }
+  fill_relation(m, c, rel);
+  if (!gamma) return RD_OK;
+  if (cap < (int64_t)c.j + 1) return RD_ERR_ARG;
+  gamma[0] = RD_GAMMA_UNSET;
+  for (int n = 1; n <= c.j; ++n) gamma[n] = c.gamma[(size_t)n];
+  return RD_OK;
+}
+
+extern "C" rd_status rd_gamma_R_import(const rd_relation_t* rel, const int64_t* gamma) {
+  if (!rd::relation_ok(rel, gamma)) return RD_ERR_ARG;
+  Cached c;
+  c.valid = true;
+  c.found = rel->found == 1;
+  c.k = rel->k;
+  c.p = rel->p;
+  c.q = rel->q;
+  c.j = rel->j;
+  c.gamma.assign(gamma, gamma + rel->j + 1);
+  c.gamma[0] = RD_GAMMA_UNSET;
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  g_cache[rel->m] = std::move(c);
+  return RD_OK;
+}

@@ -166,4 +166,8 @@ cudaError_t runs_step(const RunDesc* runs, int count, int R, cudaStream_t s);
 void set_cuda_error(cudaError_t e);
 bool aligned16(const void* p);
 
+// A relation record (rd_relation_t) and its gamma[0..j] pass the checks every record of a transfer
+// matrix satisfies (power.cu; rd_gamma_R_import states them).
+bool relation_ok(const rd_relation_t* rel, const int64_t* gamma);
+
 }  // namespace rd

@@ -484,6 +484,43 @@ extern "C" rd_status rd_server_stats(rd_server* sv, rd_server_stats_t* out) {
   return RD_OK;
 }
 
+extern "C" rd_status rd_server_export(rd_server* sv, int m, rd_relation_t* rel, int64_t* gamma, int64_t cap) {
+  if (!sv || m < 1 || m > RD_MAX_M || !rel) return RD_ERR_ARG;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  const Final& f = sv->final_[m];
+  if (!f.valid) return RD_NOT_FOUND;
+  if (f.status != RD_OK) return f.status;
+  *rel = rd_relation_t{};
+  rel->m = m;
+  rel->found = f.found ? 1 : 0;
+  rel->k = f.found ? f.k : 0;
+  rel->p = f.found ? f.p : 0;
+  rel->q = f.found ? f.q : 0;
+  rel->j = f.j;
+  if (!gamma) return RD_OK;
+  if (cap < (int64_t)f.j + 1) return RD_ERR_ARG;
+  gamma[0] = RD_GAMMA_UNSET;
+  for (int n = 1; n <= f.j; ++n) gamma[n] = f.gamma[(size_t)n];
+  return RD_OK;
+}
+
+extern "C" rd_status rd_server_import(rd_server* sv, const rd_relation_t* rel, const int64_t* gamma) {
+  if (!sv || !rd::relation_ok(rel, gamma)) return RD_ERR_ARG;
+  Final f;
+  f.valid = true;
+  f.found = rel->found == 1;
+  f.status = RD_OK;
+  f.k = rel->k;
+  f.p = rel->p;
+  f.q = rel->q;
+  f.j = rel->j;
+  f.gamma.assign(gamma, gamma + rel->j + 1);
+  f.gamma[0] = RD_GAMMA_UNSET;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  sv->final_[rel->m] = std::move(f);
+  return RD_OK;
+}
+
 extern "C" rd_status rd_server_destroy(rd_server* sv) {
   if (!sv) return RD_ERR_ARG;
   {
