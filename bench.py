@@ -715,9 +715,38 @@ def serving(rd, queries: int = 3000, rates=(1e3, 1e4, 1e5, 1e6), seed: int = 7, 
         warm = serve_stream(rd, ms, ns, arrivals, budget_gb, server=sv)
         warm.pop("gamma")
         out["warm_at_max_rate"] = warm
+        out["restart_from_records"] = restart_from_records(rd, sv, ms, ns, arrivals, budget_gb, want)
     finally:
         sv.close()
     return out
+
+
+def restart_from_records(rd, sv, ms, ns, arrivals, budget_gb: float, want) -> dict:
+    """Checkpoint and resume: the settled server's relation records (first repeat and gamma table per m)
+    go to a JSON file; a fresh server imports them and serves the same stream at the highest rate with no
+    period search at all (jobs = 0).  The answers must equal the plain path's."""
+    import tempfile
+
+    from paper_2409_17658_gb300 import relations
+
+    t0 = time.perf_counter()
+    recs = [sv.export_relation(int(m)) for m in sorted(set(ms.tolist()))]
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "relations.json")
+        relations.save(path, recs)
+        nbytes = os.path.getsize(path)
+        loaded = relations.load(path)
+    fresh = rd.Server(hbm_budget_bytes=int(budget_gb * (1 << 30)), kmax=128)
+    try:
+        for r in loaded:
+            fresh.import_relation(r)
+        t_ckpt = time.perf_counter() - t0
+        r = serve_stream(rd, ms, ns, arrivals, budget_gb, server=fresh)
+    finally:
+        fresh.close()
+    g = r.pop("gamma")
+    return {**r, "answers_equal_plain": bool(np.array_equal(g, want)), "records": len(recs), "file_bytes": nbytes,
+            "export_save_load_import_ms": t_ckpt * 1e3}
 
 
 def run_reference(args, rank, world) -> None:
