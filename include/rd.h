@@ -434,6 +434,23 @@ rd_status rd_split_minplus(const rd_split_info_t *info, const void *plan_dev, co
                            int16_t *X_dev, int64_t ldx, int16_t *C, int64_t ldc, int32_t *min_out, cudaStream_t s);
 
 /*
+ * rd_split_check_flags -- the index checks of a checked build of this library
+ * (compiled with -DRD_CHECKED; paper_2409_17658_gb300.build.build(checked=True)
+ * makes librd_checked.so).  In such a build the row-split passes (the kernels of
+ * rd_split_minplus and of the period searches that step with it) test every
+ * index they take from plan data before using it and skip the access when the
+ * test fails, OR-ing one bit per kind into a device word: 1 an input row (a word
+ * of B, resp. a row of X) past the operand, 2 a staged-row number in a list past
+ * the fiber's staged rows, 4 a group number or sub-list bound past the fiber's
+ * groups or list, 8 an output row past X, resp. R.  *flags receives the word of
+ * the current device; reset != 0 clears it.  Read it once the calls it should
+ * cover have completed (synchronise their streams first).  It stands in for a
+ * memory checker on GPUs where none can run.  A normal build has no checks:
+ * *flags = 0 and RD_NOT_FOUND.  RD_ERR_ARG for a null flags.
+ */
+rd_status rd_split_check_flags(uint32_t *flags, int reset);
+
+/*
  * rd_power_until_periodic_split -- rd_power_until_periodic (same work buffer,
  * outputs and errors) for A = A(G) of the plan's m, with the power step
  * R = A (x) P_k run by the two passes of rd_split_minplus.  A_dev (N x N,

@@ -44,91 +44,112 @@ def _lib():
     if _LIB is None:
         if not os.path.exists(LIB_PATH):
             raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2409_17658_gb300.build.build()")
-        lib = ctypes.CDLL(LIB_PATH)
-        i64, i32, vp, sz = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t
-        st = ctypes.c_int
-        lib.rd_last_cuda_error.restype = ctypes.c_char_p
-        lib.rd_last_cuda_error.argtypes = []
-        lib.rd_state_count.argtypes = [ctypes.c_int, vp]
-        lib.rd_padded_dim.argtypes = [i64, vp]
-        lib.rd_enumerate_states.argtypes = [ctypes.c_int, vp, vp, vp]
-        lib.rd_build_transfer.argtypes = [ctypes.c_int, vp, i64, vp]
-        lib.rd_build_transfer_loss.argtypes = [ctypes.c_int, vp, i64, vp]
-        lib.rd_minplus_gemm_batched.argtypes = [vp, ctypes.c_int, vp]
-        lib.rd_minplus_gemv.argtypes = [vp, vp, i64, vp, i64, i64, vp, vp]
-        lib.rd_power_until_periodic_multi.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
-        lib.rd_power_until_periodic_multi_bounded.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                                              ctypes.c_uint32, ctypes.c_int32, vp]
-        lib.rd_power_until_periodic_multi_bounded.restype = st
-        lib.rd_server_create.argtypes = [sz, ctypes.c_int, vp]
-        lib.rd_server_submit.argtypes = [vp, ctypes.c_int, vp, vp, vp]
-        lib.rd_server_wait.argtypes = [vp, ctypes.c_int, vp, ctypes.c_double, vp, vp, vp]
-        lib.rd_server_stats.argtypes = [vp, vp]
-        lib.rd_server_destroy.argtypes = [vp]
-        lib.rd_minplus_gemm.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, vp, vp]
-        lib.rd_power_work_bytes.argtypes = [i64, i64, ctypes.c_int, ctypes.c_int, vp]
-        lib.rd_power_until_periodic.argtypes = [vp, i64, i64, ctypes.c_int, vp, sz, vp, vp, vp, vp, vp]
-        lib.rd_gamma_R.argtypes = [ctypes.c_int, i64, vp]
-        lib.rd_power_slot.argtypes = [i64, i64, ctypes.c_int, sz, ctypes.c_int, vp]
-        lib.rd_power_until_periodic_noalloc.argtypes = [vp, i64, i64, ctypes.c_int, vp, vp, vp, vp, vp]
-        lib.rd_sparse_count.argtypes = [vp, i64, i64, i64, ctypes.c_int, vp, vp, vp]
-        lib.rd_sparse_record_words.argtypes = [ctypes.c_int]
-        lib.rd_sparse_record_words.restype = ctypes.c_int
-        lib.rd_sparse_build.argtypes = [vp, i64, i64, i64, ctypes.c_int, vp, vp, vp]
-        lib.rd_sparse_minplus.argtypes = [ctypes.c_int, i64, vp, vp, vp, i64, i64, vp, i64, vp, vp]
-        lib.rd_power_until_periodic_sparse.argtypes = [vp, i64, i64, ctypes.c_int, vp, vp, ctypes.c_int, vp, sz, vp,
-                                                       vp, vp, vp, vp]
-        lib.rd_sparse_tune.argtypes = [vp, i64, i64, vp, sz, vp, vp, vp]
-        lib.rd_sparse_minplus_tma.argtypes = [ctypes.c_int, i64, vp, vp, vp, i64, i64, vp, i64, vp, vp, vp]
-        lib.rd_sparse_minplus_tma_bounded.argtypes = [ctypes.c_int, i64, vp, vp, vp, i64, i64, vp, i64, vp, vp,
-                                                      ctypes.c_uint32, ctypes.c_int32, vp]
-        lib.rd_sparse_minplus_tma_bounded.restype = st
-        lib.rd_split_default_j.argtypes = [ctypes.c_int]
-        lib.rd_split_default_j.restype = ctypes.c_int
-        lib.rd_split_plan_bytes.argtypes = [ctypes.c_int, ctypes.c_int, vp]
-        lib.rd_split_plan.argtypes = [ctypes.c_int, ctypes.c_int, vp, sz, vp, vp]
-        lib.rd_split_minplus.argtypes = [vp, vp, vp, i64, vp, i64, vp, i64, vp, vp]
-        lib.rd_power_until_periodic_split.argtypes = [vp, i64, vp, vp, vp, i64, ctypes.c_int, vp, sz, vp, vp, vp,
-                                                      vp, vp]
-        lib.rd_tune_bucket.argtypes = [i64]
-        lib.rd_tune_bucket.restype = ctypes.c_int
-        lib.rd_tune_set.argtypes = [vp, ctypes.c_int]
-        lib.rd_tune_get.argtypes = [vp, ctypes.c_int, vp]
-        lib.rd_tune_lookup.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
-        lib.rd_tune_gemm.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, ctypes.c_int, vp, vp]
-        lib.rd_tune_split.argtypes = [vp, vp, vp, i64, vp, i64, vp, i64, ctypes.c_int, vp, vp]
-        for name in ("rd_tune_set", "rd_tune_get", "rd_tune_lookup", "rd_tune_gemm", "rd_tune_split"):
-            getattr(lib, name).restype = st
-        for name in ("rd_state_count", "rd_padded_dim", "rd_enumerate_states", "rd_build_transfer",
-                     "rd_minplus_gemm", "rd_power_work_bytes", "rd_power_until_periodic", "rd_gamma_R",
-                     "rd_power_slot", "rd_power_until_periodic_noalloc", "rd_sparse_count", "rd_sparse_build",
-                     "rd_sparse_minplus", "rd_power_until_periodic_sparse", "rd_sparse_tune",
-                     "rd_build_transfer_loss", "rd_minplus_gemm_batched", "rd_power_until_periodic_multi",
-                     "rd_server_create", "rd_server_submit", "rd_server_wait", "rd_server_stats",
-                     "rd_server_destroy", "rd_sparse_minplus_tma", "rd_minplus_gemv", "rd_split_plan_bytes",
-                     "rd_split_plan", "rd_split_minplus", "rd_power_until_periodic_split",
-                     "rd_measure_addmin_peak"):
-            getattr(lib, name).restype = st
-        lib.rd_measure_addmin_peak.argtypes = [vp, sz, i64, vp, vp]
-        lib.rd_gamma_R_clear.argtypes = []
-        lib.rd_gamma_R_clear.restype = st
-        lib.rd_minplus_gemm_streamk_work_bytes.argtypes = [i64, i64, i64, vp]
-        lib.rd_minplus_gemm_streamk_work_bytes.restype = st
-        lib.rd_minplus_gemm_streamk.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, vp, sz, vp, vp]
-        lib.rd_minplus_gemm_streamk.restype = st
-        lib.rd_minplus_gemm_host_work_bytes.argtypes = [i64, i64, i64, vp]
-        lib.rd_minplus_gemm_host_work_bytes.restype = st
-        lib.rd_minplus_gemm_host.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, vp, sz, vp, vp]
-        lib.rd_minplus_gemm_host.restype = st
-        lib.rd_gamma_R_export.argtypes = [ctypes.c_int, vp, vp, i64]
-        lib.rd_gamma_R_import.argtypes = [vp, vp]
-        lib.rd_server_export.argtypes = [vp, ctypes.c_int, vp, vp, i64]
-        lib.rd_server_import.argtypes = [vp, vp, vp]
-        for name in ("rd_gamma_R_export", "rd_gamma_R_import", "rd_server_export", "rd_server_import"):
-            getattr(lib, name).restype = st
-        _ = i32
-        _LIB = lib
+        _LIB = _configure(ctypes.CDLL(LIB_PATH))
     return _LIB
+
+
+def use_library(path: str):
+    """Route every call of this binding to the library at `path` (for example the checked build,
+    build.build(checked=True)); returns the library used before, for restoring with use_library_handle."""
+    global _LIB
+    prev = _LIB
+    _LIB = _configure(ctypes.CDLL(path))
+    return prev
+
+
+def use_library_handle(lib) -> None:
+    """Restore a library returned by use_library (None: the default librd.so on next use)."""
+    global _LIB
+    _LIB = lib
+
+
+def _configure(lib):
+    """Declares the argument and result types of every entry point of a loaded library."""
+    i64, i32, vp, sz = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t
+    st = ctypes.c_int
+    lib.rd_last_cuda_error.restype = ctypes.c_char_p
+    lib.rd_last_cuda_error.argtypes = []
+    lib.rd_state_count.argtypes = [ctypes.c_int, vp]
+    lib.rd_padded_dim.argtypes = [i64, vp]
+    lib.rd_enumerate_states.argtypes = [ctypes.c_int, vp, vp, vp]
+    lib.rd_build_transfer.argtypes = [ctypes.c_int, vp, i64, vp]
+    lib.rd_build_transfer_loss.argtypes = [ctypes.c_int, vp, i64, vp]
+    lib.rd_minplus_gemm_batched.argtypes = [vp, ctypes.c_int, vp]
+    lib.rd_minplus_gemv.argtypes = [vp, vp, i64, vp, i64, i64, vp, vp]
+    lib.rd_power_until_periodic_multi.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
+    lib.rd_power_until_periodic_multi_bounded.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                          ctypes.c_uint32, ctypes.c_int32, vp]
+    lib.rd_power_until_periodic_multi_bounded.restype = st
+    lib.rd_server_create.argtypes = [sz, ctypes.c_int, vp]
+    lib.rd_server_submit.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    lib.rd_server_wait.argtypes = [vp, ctypes.c_int, vp, ctypes.c_double, vp, vp, vp]
+    lib.rd_server_stats.argtypes = [vp, vp]
+    lib.rd_server_destroy.argtypes = [vp]
+    lib.rd_minplus_gemm.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, vp, vp]
+    lib.rd_power_work_bytes.argtypes = [i64, i64, ctypes.c_int, ctypes.c_int, vp]
+    lib.rd_power_until_periodic.argtypes = [vp, i64, i64, ctypes.c_int, vp, sz, vp, vp, vp, vp, vp]
+    lib.rd_gamma_R.argtypes = [ctypes.c_int, i64, vp]
+    lib.rd_power_slot.argtypes = [i64, i64, ctypes.c_int, sz, ctypes.c_int, vp]
+    lib.rd_power_until_periodic_noalloc.argtypes = [vp, i64, i64, ctypes.c_int, vp, vp, vp, vp, vp]
+    lib.rd_sparse_count.argtypes = [vp, i64, i64, i64, ctypes.c_int, vp, vp, vp]
+    lib.rd_sparse_record_words.argtypes = [ctypes.c_int]
+    lib.rd_sparse_record_words.restype = ctypes.c_int
+    lib.rd_sparse_build.argtypes = [vp, i64, i64, i64, ctypes.c_int, vp, vp, vp]
+    lib.rd_sparse_minplus.argtypes = [ctypes.c_int, i64, vp, vp, vp, i64, i64, vp, i64, vp, vp]
+    lib.rd_power_until_periodic_sparse.argtypes = [vp, i64, i64, ctypes.c_int, vp, vp, ctypes.c_int, vp, sz, vp,
+                                                   vp, vp, vp, vp]
+    lib.rd_sparse_tune.argtypes = [vp, i64, i64, vp, sz, vp, vp, vp]
+    lib.rd_sparse_minplus_tma.argtypes = [ctypes.c_int, i64, vp, vp, vp, i64, i64, vp, i64, vp, vp, vp]
+    lib.rd_sparse_minplus_tma_bounded.argtypes = [ctypes.c_int, i64, vp, vp, vp, i64, i64, vp, i64, vp, vp,
+                                                  ctypes.c_uint32, ctypes.c_int32, vp]
+    lib.rd_sparse_minplus_tma_bounded.restype = st
+    lib.rd_split_default_j.argtypes = [ctypes.c_int]
+    lib.rd_split_default_j.restype = ctypes.c_int
+    lib.rd_split_plan_bytes.argtypes = [ctypes.c_int, ctypes.c_int, vp]
+    lib.rd_split_plan.argtypes = [ctypes.c_int, ctypes.c_int, vp, sz, vp, vp]
+    lib.rd_split_minplus.argtypes = [vp, vp, vp, i64, vp, i64, vp, i64, vp, vp]
+    lib.rd_power_until_periodic_split.argtypes = [vp, i64, vp, vp, vp, i64, ctypes.c_int, vp, sz, vp, vp, vp,
+                                                  vp, vp]
+    lib.rd_tune_bucket.argtypes = [i64]
+    lib.rd_tune_bucket.restype = ctypes.c_int
+    lib.rd_tune_set.argtypes = [vp, ctypes.c_int]
+    lib.rd_tune_get.argtypes = [vp, ctypes.c_int, vp]
+    lib.rd_tune_lookup.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
+    lib.rd_tune_gemm.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, ctypes.c_int, vp, vp]
+    lib.rd_tune_split.argtypes = [vp, vp, vp, i64, vp, i64, vp, i64, ctypes.c_int, vp, vp]
+    for name in ("rd_tune_set", "rd_tune_get", "rd_tune_lookup", "rd_tune_gemm", "rd_tune_split"):
+        getattr(lib, name).restype = st
+    for name in ("rd_state_count", "rd_padded_dim", "rd_enumerate_states", "rd_build_transfer",
+                 "rd_minplus_gemm", "rd_power_work_bytes", "rd_power_until_periodic", "rd_gamma_R",
+                 "rd_power_slot", "rd_power_until_periodic_noalloc", "rd_sparse_count", "rd_sparse_build",
+                 "rd_sparse_minplus", "rd_power_until_periodic_sparse", "rd_sparse_tune",
+                 "rd_build_transfer_loss", "rd_minplus_gemm_batched", "rd_power_until_periodic_multi",
+                 "rd_server_create", "rd_server_submit", "rd_server_wait", "rd_server_stats",
+                 "rd_server_destroy", "rd_sparse_minplus_tma", "rd_minplus_gemv", "rd_split_plan_bytes",
+                 "rd_split_plan", "rd_split_minplus", "rd_power_until_periodic_split",
+                 "rd_measure_addmin_peak"):
+        getattr(lib, name).restype = st
+    lib.rd_measure_addmin_peak.argtypes = [vp, sz, i64, vp, vp]
+    lib.rd_gamma_R_clear.argtypes = []
+    lib.rd_gamma_R_clear.restype = st
+    lib.rd_minplus_gemm_streamk_work_bytes.argtypes = [i64, i64, i64, vp]
+    lib.rd_minplus_gemm_streamk_work_bytes.restype = st
+    lib.rd_minplus_gemm_streamk.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, vp, sz, vp, vp]
+    lib.rd_minplus_gemm_streamk.restype = st
+    lib.rd_minplus_gemm_host_work_bytes.argtypes = [i64, i64, i64, vp]
+    lib.rd_minplus_gemm_host_work_bytes.restype = st
+    lib.rd_minplus_gemm_host.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, vp, sz, vp, vp]
+    lib.rd_minplus_gemm_host.restype = st
+    lib.rd_gamma_R_export.argtypes = [ctypes.c_int, vp, vp, i64]
+    lib.rd_gamma_R_import.argtypes = [vp, vp]
+    lib.rd_server_export.argtypes = [vp, ctypes.c_int, vp, vp, i64]
+    lib.rd_server_import.argtypes = [vp, vp, vp]
+    for name in ("rd_gamma_R_export", "rd_gamma_R_import", "rd_server_export", "rd_server_import"):
+        getattr(lib, name).restype = st
+    lib.rd_split_check_flags.argtypes = [vp, ctypes.c_int]
+    lib.rd_split_check_flags.restype = st
+    _ = i32
+    return lib
 
 
 def declared_symbols() -> list[str]:
@@ -574,6 +595,17 @@ class SplitInfo(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def split_check_flags(reset: bool = True) -> int | None:
+    """rd_split_check_flags: the row-split passes' index-check bits of the current device (checked build),
+    or None for a library built without checks."""
+    v = ctypes.c_uint32()
+    st = _lib().rd_split_check_flags(ctypes.byref(v), 1 if reset else 0)
+    if st == RD_NOT_FOUND:
+        return None
+    _check(st, "rd_split_check_flags")
+    return v.value
 
 
 def split_default_j(m: int) -> int:

@@ -534,6 +534,7 @@ struct SplitPass {
   int16_t* out;  // pass 1: X;  pass 2: R
   int64_t ldout;
   int64_t ncols;           // columns of this launch (a chunk of the N columns)
+  int64_t in_rows, out_rows;  // rows of `in` and `out` (pass 1: N and X rows; pass 2: X rows and N)
   int64_t in_col0, out_col0;  // first column of the chunk in `in` resp. `out` (X holds one chunk at column 0)
   int32_t n_groups;
   int32_t norm;           // ring mode: pass 1 reduces the next offset step mu into st->mu, pass 2 writes
@@ -557,6 +558,21 @@ struct SplitPass {
 };
 
 __device__ __forceinline__ uint32_t min3(uint32_t a, uint32_t b, uint32_t c) { return __vimin3_s16x2(a, b, c); }
+
+// Checked builds (-DRD_CHECKED, rd_split_check_flags): every index the passes take from plan data -- input
+// rows, staged-row numbers in the lists, group numbers and sub-list bounds, output rows -- is tested against
+// its buffer; a failed test ORs its bit into g_split_check and the access is skipped (an RD_INF row read
+// instead, no write).  In other builds split_ok is constant true and the tests compile away.
+constexpr unsigned kChkInRow = 1, kChkSlot = 2, kChkGroup = 4, kChkOutRow = 8;
+#ifdef RD_CHECKED
+__device__ unsigned int g_split_check = 0;
+__device__ __forceinline__ bool split_ok(bool c, unsigned bit) {
+  if (!c) atomicOr(&g_split_check, bit);
+  return c;
+}
+#else
+__device__ __forceinline__ bool split_ok(bool, unsigned) { return true; }
+#endif
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
@@ -595,7 +611,7 @@ __device__ __forceinline__ void fold_quad(uint4 (&acc)[4], const uint4& v0, cons
 // memory), so a row's address is one add and one mask or shift away.
 template <int SET, int LR, bool SCALED>
 __device__ __forceinline__ void fold_sublist(uint4 (&acc)[4], const uint4* sm, const uint32_t* pairs, int e0, int e1,
-                                             int lane) {
+                                             int lane, uint32_t nst) {
   int p = e0 >> 1;
   const int pe = e1 >> 1;
   if constexpr (SCALED) {
@@ -616,7 +632,9 @@ __device__ __forceinline__ void fold_sublist(uint4 (&acc)[4], const uint4* sm, c
     }
   } else {
   for (; p + 2 <= pe; p += 2) {
-    const uint32_t i0 = pairs[p], i1 = pairs[p + 1];
+    uint32_t i0 = pairs[p], i1 = pairs[p + 1];
+    if (!split_ok((i0 & 0xFFFFu) < nst && (i0 >> 16) < nst && (i1 & 0xFFFFu) < nst && (i1 >> 16) < nst, kChkSlot))
+      i0 = i1 = 0;  // the RD_INF dummy row
     const uint4 v0 = sm[(int)(i0 & 0xFFFFu) * LR + lane];
     const uint4 v1 = sm[(int)(i0 >> 16) * LR + lane];
     const uint4 v2 = sm[(int)(i1 & 0xFFFFu) * LR + lane];
@@ -625,7 +643,8 @@ __device__ __forceinline__ void fold_sublist(uint4 (&acc)[4], const uint4* sm, c
     fold_pair<SET>(acc, v2, v3);
   }
   if (p < pe) {
-    const uint32_t i0 = pairs[p];
+    uint32_t i0 = pairs[p];
+    if (!split_ok((i0 & 0xFFFFu) < nst && (i0 >> 16) < nst, kChkSlot)) i0 = 0;
     fold_pair<SET>(acc, sm[(int)(i0 & 0xFFFFu) * LR + lane], sm[(int)(i0 >> 16) * LR + lane]);
   }
   }
@@ -688,6 +707,11 @@ __device__ __forceinline__ void split_pass_body(const SplitPass& a, const int64_
   const uint32_t* glst = reinterpret_cast<const uint32_t*>(a.lst) + (base >> 1);
   const int32_t f0 = __ldg(a.fstart + f);
   const int nst = __ldg(a.fstart + f + 1) - f0 + 1;  // row 0 is the dummy, rows 1..n the slots
+#ifdef RD_CHECKED
+  const int list_pairs = (__ldg(a.gls + r0 + (int64_t)a.n_groups * kRec) - base) >> 1;
+#else
+  constexpr int list_pairs = 0;  // used by the checks only
+#endif
   if (STAGED) {
     const int nb = a.n_groups * kRec;
     for (int i = threadIdx.x; i < nb; i += kSplitThreads) sgls[i] = (uint16_t)(__ldg(a.gls + r0 + i) - base);
@@ -695,7 +719,8 @@ __device__ __forceinline__ void split_pass_body(const SplitPass& a, const int64_
     const int npairs = (__ldg(a.gls + r0 + nb) - base) >> 1;
     constexpr uint32_t kRowBytes = (uint32_t)W * 2;  // staged rows fit in 64 KB (stageable), so offsets fit 16 bits
     for (int i = threadIdx.x; i < npairs; i += kSplitThreads) {
-      const uint32_t q = __ldg(glst + i);
+      uint32_t q = __ldg(glst + i);
+      if (!split_ok((q & 0xFFFFu) < (uint32_t)nst && (q >> 16) < (uint32_t)nst, kChkSlot)) q = 0;
       slst[i] = (q & 0xFFFFu) * kRowBytes | ((q >> 16) * kRowBytes) << 16;
     }
     if (FIRST)
@@ -726,7 +751,7 @@ __device__ __forceinline__ void split_pass_body(const SplitPass& a, const int64_
 #pragma unroll 1
     for (int s = gi; s < nst; s += G) {
       const int32_t e = (s < 1) ? -1 : FIRST ? (STAGED ? smem_words[s - 1] : __ldg(a.fmem + f0 + s - 1)) : f0 + s - 1;
-      if (ok && e >= 0)
+      if (ok && e >= 0 && split_ok((int64_t)(FIRST ? (e >> 5) : e) < a.in_rows, kChkInRow))
         cp_async16(&sm[s * LR + lane], in + (int64_t)(FIRST ? (e >> 5) : e) * a.ldin + c);
       else
         sm[s * LR + lane] = inf4;
@@ -756,7 +781,8 @@ __device__ __forceinline__ void split_pass_body(const SplitPass& a, const int64_
     for (int round0 = 0; round0 < a.n_groups; round0 += G) {
       const int idx = round0 + (((round0 / G) & 1) ? (G - 1 - gi) : gi);
       if (idx >= a.n_groups) continue;
-      const int g = STAGED ? sord[idx] : __ldg(gord + idx);
+      int g = STAGED ? sord[idx] : __ldg(gord + idx);
+      if (!split_ok(g < a.n_groups, kChkGroup)) continue;
       uint4 acc[4] = {inf4, inf4, inf4, inf4};
       // the group's record: the starts of its 7 sub-lists and their end
       int b[kRec];
@@ -770,20 +796,26 @@ __device__ __forceinline__ void split_pass_body(const SplitPass& a, const int64_
         b[0] = q0.x - base; b[1] = q0.y - base; b[2] = q0.z - base; b[3] = q0.w - base;
         b[4] = q1.x - base; b[5] = q1.y - base; b[6] = q1.z - base; b[7] = q1.w - base;
       }
-      fold_sublist<0x1, LR, STAGED>(acc, sm, pairs, b[0], b[1], lane);
-      fold_sublist<0x4, LR, STAGED>(acc, sm, pairs, b[1], b[2], lane);
-      fold_sublist<0x5, LR, STAGED>(acc, sm, pairs, b[2], b[3], lane);
-      fold_sublist<0x6, LR, STAGED>(acc, sm, pairs, b[3], b[4], lane);
-      fold_sublist<0x7, LR, STAGED>(acc, sm, pairs, b[4], b[5], lane);
-      fold_sublist<0xC, LR, STAGED>(acc, sm, pairs, b[5], b[6], lane);
-      fold_sublist<0xD, LR, STAGED>(acc, sm, pairs, b[6], b[7], lane);
+      {
+        bool rec_ok = b[0] >= 0 && b[7] <= 2 * list_pairs;
+#pragma unroll
+        for (int q = 0; q < kRec - 1; ++q) rec_ok = rec_ok && b[q] <= b[q + 1];
+        if (!split_ok(rec_ok, kChkGroup)) continue;
+      }
+      fold_sublist<0x1, LR, STAGED>(acc, sm, pairs, b[0], b[1], lane, (uint32_t)nst);
+      fold_sublist<0x4, LR, STAGED>(acc, sm, pairs, b[1], b[2], lane, (uint32_t)nst);
+      fold_sublist<0x5, LR, STAGED>(acc, sm, pairs, b[2], b[3], lane, (uint32_t)nst);
+      fold_sublist<0x6, LR, STAGED>(acc, sm, pairs, b[3], b[4], lane, (uint32_t)nst);
+      fold_sublist<0x7, LR, STAGED>(acc, sm, pairs, b[4], b[5], lane, (uint32_t)nst);
+      fold_sublist<0xC, LR, STAGED>(acc, sm, pairs, b[5], b[6], lane, (uint32_t)nst);
+      fold_sublist<0xD, LR, STAGED>(acc, sm, pairs, b[6], b[7], lane, (uint32_t)nst);
       if (!ok) continue;
       const int4 rows = STAGED ? sgo[g] : __ldg(go4 + g);
       const int32_t row4[4] = {rows.x, rows.y, rows.z, rows.w};
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
         const int64_t row = row4[l];
-        if (row < 0) continue;
+        if (row < 0 || !split_ok(row < a.out_rows, kChkOutRow)) continue;
         if (FIRST) {
           *reinterpret_cast<uint4*>(out + row * a.ldout + c) = acc[l];
         } else {
@@ -1028,6 +1060,8 @@ void passes_of(const rd_split_info_t& info, const void* plan, SplitPass* p1, Spl
   *p1 = SplitPass{};
   *p2 = SplitPass{};
   p1->ncols = p2->ncols = info.N;
+  p1->in_rows = p2->out_rows = info.N;
+  p1->out_rows = p2->in_rows = info.x_rows;
   p1->n_groups = (int32_t)L.nG1;
   p1->max_slots = info.slots1;
   p1->max_list = info.lmax1;
@@ -1532,4 +1566,26 @@ extern "C" rd_status rd_power_until_periodic_split(const int16_t* A_dev, int64_t
   *p_out = h.found_j - h.found_i;
   *q_out = off_j - off_i;
   return RD_OK;
+}
+
+extern "C" rd_status rd_split_check_flags(uint32_t* flags, int reset) {
+  if (!flags) return RD_ERR_ARG;
+  *flags = 0;
+#ifdef RD_CHECKED
+  unsigned int v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_split_check, sizeof(v));
+  if (e == cudaSuccess && reset) {
+    const unsigned int zero = 0;
+    e = cudaMemcpyToSymbol(g_split_check, &zero, sizeof(zero));
+  }
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return RD_ERR_CUDA;
+  }
+  *flags = v;
+  return RD_OK;
+#else
+  (void)reset;
+  return RD_NOT_FOUND;
+#endif
 }

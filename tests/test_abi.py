@@ -98,3 +98,9 @@ def test_split_plan_sizes(rd):
     assert all(0 < v < 256 << 20 for v in b.values())
     assert min(b, key=b.get) == rd.split_default_j(10) and b[5] < 64 << 20
     assert rd.split_plan_bytes(2, 1) < rd.split_plan_bytes(3, 1) < rd.split_plan_bytes(4, 2)
+
+
+def test_split_check_flags_absent_in_the_normal_build(rd):
+    """The normal build compiles no index checks: rd_split_check_flags answers RD_NOT_FOUND with no CUDA call."""
+    assert rd.split_check_flags() is None
+    assert rd._lib().rd_split_check_flags(None, 0) == rd.RD_ERR_ARG
