@@ -165,3 +165,23 @@ def test_relation_file_round_trip(rd, orc, tmp_path):
     bad.write_text('{"format": "rd-tune-1", "entries": []}')
     with pytest.raises(ValueError):
         relations.load(str(bad))
+
+
+def test_command_line_answers_from_a_relation_file(rd, tmp_path):
+    """python -m paper_2409_17658_gb300 gamma M N --relations FILE answers on the host from the saved record
+    (no GPU here); m = 9 against the closed form printed in Sec. 4.C."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    from paper_2409_17658_gb300 import relations
+
+    path = str(tmp_path / "rel.json")
+    relations.save(path, [golden_record(9)])
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    ns = [3, 7, 27, 28, 500, 12345]
+    out = subprocess.run([sys.executable, "-m", "paper_2409_17658_gb300", "gamma", "9", *map(str, ns), "--relations",
+                          path], cwd=root, capture_output=True, text=True, check=True).stdout
+    got = [json.loads(line)["gamma_R"] for line in out.splitlines()]
+    assert got == [4 * n if n % 5 == 0 else 4 * n + 2 for n in ns]
