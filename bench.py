@@ -990,7 +990,7 @@ def main() -> None:
     if rank == 0:
         extra["tuning_table"] = rd.tune_table()
     if rank == 0 and not args.no_cpu:
-        extra["cpu_baseline"] = cpu_baseline_gemm(a, b, rows=32)
+        extra["cpu_baseline"] = cpu_baseline_gemm(a, b, rows=128)  # about 10 s of CPU work on 16 cores
 
     if rank == 0:
         achieved = ops_per_step / (per_launch_ms * 1e-3) / 1e9
