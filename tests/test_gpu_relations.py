@@ -90,3 +90,21 @@ def test_server_export_after_a_search(rd, orc):
         with pytest.raises(rd.RdError) as e:
             sv.import_relation(dict(oracle_record(orc, 5), q=13))  # gamma[k + p] != gamma[k] + q
         assert e.value.status == rd.RD_ERR_ARG
+
+
+def test_server_import_while_its_search_runs(rd, orc):
+    """A record imported for an m whose search is already running: queries routed after the import are
+    answered from it, the running search still completes, and every answer (before, during and after)
+    equals Prop. 7 from the oracle's first repeat."""
+    import numpy as np
+
+    rec = golden_record(9)
+    with rd.Server(hbm_budget_bytes=32 << 30) as sv:
+        first = sv.submit([9] * 4, [30, 31, 500, 1001])  # starts the m = 9 search
+        sv.import_relation(rec)
+        second = sv.submit([9] * 4, [3, 27, 28, 12345])
+        g, st, _ = sv.wait(np.concatenate([first, second]), timeout_s=120)
+        assert (st == rd.RD_OK).all()
+        ns = [30, 31, 500, 1001, 3, 27, 28, 12345]
+        assert [int(x) for x in g] == [closed_form(rec, n) for n in ns]
+        assert sv.export_relation(9) == rec
