@@ -605,7 +605,28 @@ def batched_products(rd, torch, count: int = 64, seed: int = 4) -> dict:
                               "same_results": (timings["sequential_triples"] == timings["together_graph_triples"] ==
                                                timings["together_graph_launches_per_phase_triples"]),
                               "triples": timings["together_graph_triples"]}
-    del runs
+    # the runs that the persistent step kernel carries alone (m = 1..7, sparse step): one launch per step for
+    # all seven, eight steps per replay of the captured graph, against each search on its own
+    small = runs[:7]
+    t_small = {}
+    for name in ("sequential", "together"):
+        for _ in range(2):  # first pass untimed
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if name == "sequential":
+                res = [one(*run) for run in small]
+            else:
+                res = rd.power_until_periodic_multi(small, R, kmax, graph_steps=8)
+            torch.cuda.synchronize()
+            t_small[name] = time.perf_counter() - t0
+        t_small[name + "_triples"] = [(r["k"], r["p"], r["q"]) for r in res]
+    out["periods_m1_to_7_one_launch"] = {
+        "sequential_s": t_small["sequential"], "together_graph_s": t_small["together"],
+        "speedup": t_small["sequential"] / t_small["together"], "launches_per_step": 1,
+        "launches_how": "one multi_step_kernel launch per step for all seven runs, 8 steps per graph replay; "
+                        "alone, m <= 4 run the single-CTA search and m = 5..7 the sparse step",
+        "same_results": t_small["sequential_triples"] == t_small["together_triples"]}
+    del runs, small
     torch.cuda.empty_cache()
     return out
 
