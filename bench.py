@@ -268,6 +268,14 @@ def time_to_period(rd, torch, ms: list[int], with_oracle: bool) -> dict:
                 o = oracle.power_until_periodic(m, kmax=kmax)
                 entry["oracle_s"] = time.perf_counter() - t0
                 entry["oracle_matches"] = bool(o["found"] and (o["k"], o["p"], o["q"]) == (r["k"], r["p"], r["q"]))
+                # the same search on one host thread, in a child process (OpenMP reads its thread count at start)
+                code = (f"import sys, time; sys.path.insert(0, {ROOT!r}); import oracle; oracle.build(); "
+                        f"t = time.perf_counter(); oracle.power_until_periodic({m}, kmax={kmax}); "
+                        f"print(time.perf_counter() - t)")
+                one = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                                     env=dict(os.environ, OMP_NUM_THREADS="1"), timeout=600)
+                if one.returncode == 0:
+                    entry["oracle_s_one_thread"] = float(one.stdout.strip().splitlines()[-1])
             else:
                 rows = max(16, oracle.threads())  # one row per host thread at least, so every core works
                 t0 = time.perf_counter()
